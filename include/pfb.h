@@ -1,0 +1,237 @@
+/*
+ * pfb.h -- C ABI of the GB300 polyphase filter bank (PFB) channeliser.
+ *
+ * The operation (TINA, arXiv 2408.16551, Sec. 5.2 with Sec. 4.3 and 4.1):
+ *   an input stream x[n] is cut into frames of P samples, branch p of frame f
+ *   being x_p(f) = x[f*P + p]; each branch runs a T-tap FIR (the paper's
+ *   FIR-as-convolution, Sec. 4.3, in its cross-correlation form
+ *   O(w) = sum_n I(w+n) K(n)), and every spectrum of P branch sums goes
+ *   through a P-point DFT (the Fourier-matrix product Z = X F of Sec. 4.1):
+ *
+ *     y[s,p] = sum_{m<T} h[m*P + p] * x[(s+m)*P + p]            (Sec. 5.2)
+ *     X[s,k] = sum_{p<P} y[s,p] * exp(-2*pi*i*p*k/P)             (Sec. 4.1)
+ *
+ *   for s < S = max(0, floor(N/P) - T + 1) ("valid" spectra, hop P).
+ *   h[0..P*T) is the prototype filter: a symmetric window (Hann, Hamming,
+ *   Blackman) times sinc((n - (L-1)/2) / P), normalised to sum(h) = 1, or
+ *   caller-supplied taps.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are plain CUDA device addresses on the plan's device,
+ *     16-byte aligned.  The caller owns all input/output buffers; they must
+ *     stay alive until the work that uses them completes (stream order for
+ *     pfb_execute*, pfb_poll()==PFB_OK for pfb_submit).  The library owns plan
+ *     tables, batch tables and per-stream filter state.
+ *   - Errors are reported by status code only; nothing aborts or throws across
+ *     this ABI.  Arguments are validated before any launch, so an invalid call
+ *     has no effect on the device.  pfb_last_error() gives a message for the
+ *     calling thread's last failed call.
+ *   - pfb_execute* are asynchronous on the given CUDA stream (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream) and never synchronise.
+ *   - Output layout: complex64 (interleaved fp32 re, im) X[s][k], spectrum-
+ *     major, bin k contiguous (the paper's Z(m,n): m = spectrum, n = bin).
+ *   - Input layouts: PFB_IN_R32 = float32[N]; PFB_IN_C64 = complex64[N]
+ *     (interleaved re, im); PFB_IN_CI8 = int8[2N] (interleaved re, im),
+ *     dequantised in-kernel as value * in_scale.
+ */
+#ifndef PFB_H_
+#define PFB_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFB_API_VERSION 1
+
+#if defined(__GNUC__)
+#define PFB_API __attribute__((visibility("default")))
+#else
+#define PFB_API
+#endif
+
+typedef enum pfb_status {
+    PFB_OK = 0,
+    PFB_PENDING = 1,          /* pfb_poll: submitted work not finished yet */
+    PFB_ERR_INVALID = -1,     /* bad argument; nothing was launched */
+    PFB_ERR_OOM = -2,         /* device or host allocation failed */
+    PFB_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    PFB_ERR_BUSY = -4,        /* server: over budget/slots and not queuing */
+    PFB_ERR_TIMEOUT = -5,     /* a bounded wait ran out (host or device side) */
+    PFB_ERR_INTERNAL = -6,    /* a kernel reported an internal consistency error */
+    PFB_ERR_UNSUPPORTED = -7  /* valid request this build has no kernel for */
+} pfb_status;
+
+typedef enum pfb_in_dtype { PFB_IN_R32 = 0, PFB_IN_C64 = 1, PFB_IN_CI8 = 2 } pfb_in_dtype;
+
+typedef enum pfb_window {
+    PFB_WIN_HANN = 0, PFB_WIN_HAMMING = 1, PFB_WIN_BLACKMAN = 2, PFB_WIN_USER = 3
+} pfb_window;
+
+/* How the P-point DFT of Sec. 4.1 is computed. */
+typedef enum pfb_dft_path {
+    PFB_DFT_FFT_F32 = 0,      /* radix shared-memory FFT, FP32 (the fast path) */
+    PFB_DFT_GEMM_F32 = 1,     /* product with the DFT matrix, FP32 on the SIMT cores */
+    PFB_DFT_GEMM_BF16X3 = 2   /* product with the DFT matrix on the tensor cores:
+                                 y and W split into bf16 hi+lo, three products
+                                 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+} pfb_dft_path;
+
+typedef struct pfb_plan_s *pfb_plan_t;
+typedef struct pfb_batch_s *pfb_batch_t;
+typedef struct pfb_server_s *pfb_server_t;
+
+/* Plan descriptor.  P: branches = channels, a power of two in [4, 4096].
+ * T: taps per branch, 1..64.  in_scale: dequantisation factor for
+ * PFB_IN_CI8 (must be finite; ignored for other dtypes).  user_taps_host:
+ * P*T doubles (host memory, read during pfb_plan_create only) when
+ * window == PFB_WIN_USER, else NULL; user taps are used as given.
+ * device: CUDA ordinal, or -1 for the calling thread's current device. */
+typedef struct pfb_plan_desc {
+    int32_t P;
+    int32_t T;
+    int32_t in_dtype;        /* pfb_in_dtype */
+    float in_scale;
+    int32_t window;          /* pfb_window */
+    int32_t path;            /* pfb_dft_path */
+    const double *user_taps_host;
+    int32_t device;
+    int32_t reserved;        /* must be 0 */
+} pfb_plan_desc;
+
+/* Build a plan: validates the descriptor, then generates on the GPU, in FP64,
+ * the prototype filter (Sec. 5.2 taps), the FFT twiddles and, for the GEMM
+ * paths, the DFT matrix of Sec. 4.1 (bf16 hi/lo splits or fp32), and stores
+ * them in device memory owned by the plan.  Synchronises the device once.
+ * Errors: PFB_ERR_INVALID (descriptor), PFB_ERR_OOM, PFB_ERR_CUDA. */
+PFB_API pfb_status pfb_plan_create(const pfb_plan_desc *desc, pfb_plan_t *out_plan);
+
+/* Free the plan's device tables.  The caller must ensure no launched work
+ * still uses the plan.  NULL is accepted. */
+PFB_API pfb_status pfb_plan_destroy(pfb_plan_t plan);
+
+/* Spectra produced for n_samples input samples: max(0, floor(n/P) - T + 1)
+ * (Sec. 5.2 valid outputs, hop P).  Returns -1 for a NULL plan or n < 0. */
+PFB_API int64_t pfb_out_spectra(pfb_plan_t plan, int64_t n_samples);
+
+/* Copy the plan's FP64 prototype filter h[0..P*T) (as generated on the GPU)
+ * to host memory.  cap = number of doubles available at host_out. */
+PFB_API pfb_status pfb_plan_get_taps(pfb_plan_t plan, double *host_out, int64_t cap);
+
+/* Channelise one stream: X = DFT(FIR(x)) for all S valid spectra.
+ * d_in: n_samples samples in the plan's in_dtype (device memory).
+ * d_out: complex64 [out_cap_spectra][P] (device memory); S rows are written.
+ * Errors: PFB_ERR_INVALID if out_cap_spectra < S, pointers misaligned or NULL
+ * while S > 0; PFB_ERR_CUDA if the launch fails.  S == 0 is valid (no-op). */
+PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samples,
+                       void *d_out, int64_t out_cap_spectra, void *cuda_stream);
+
+/* Same as pfb_execute, from and to HOST memory: the library stages the input
+ * through device buffers it owns (host->device copy, kernel, device->host
+ * copy) on cuda_stream and returns after the output is in host_out.  Pinned
+ * host memory gives the fastest copies. */
+PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples,
+                            void *host_out, int64_t out_cap_spectra, void *cuda_stream);
+
+/* One stream of a batch. */
+typedef struct pfb_batch_item {
+    pfb_plan_t plan;
+    const void *d_in;
+    int64_t n_samples;
+    void *d_out;
+    int64_t out_cap_spectra;
+} pfb_batch_item;
+
+/* Channelise many independent streams of uneven P, T and length in one call:
+ * streams are grouped by kernel variant and each group runs as one persistent
+ * launch over the flattened list of (stream, spectrum-batch) work units.
+ * Streams producing 0 spectra are skipped.  All plans must be on one device.
+ * Results equal per-stream pfb_execute bit for bit. */
+PFB_API pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_items, void *cuda_stream);
+
+/* A reusable batch: the launches of pfb_execute_batch captured once into a
+ * CUDA graph (tile shapes from the autotuner cache), replayed by
+ * pfb_batch_launch.  The items' buffers must stay valid while the batch
+ * object is used. */
+PFB_API pfb_status pfb_batch_create(const pfb_batch_item *items, int32_t n_items, pfb_batch_t *out_batch);
+PFB_API pfb_status pfb_batch_launch(pfb_batch_t batch, void *cuda_stream);
+PFB_API pfb_status pfb_batch_destroy(pfb_batch_t batch);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of channelisation requests                */
+/* ---------------------------------------------------------------------- */
+
+/* hbm_budget_bytes: device bytes the server may hold for in-flight work and
+ * resident filter state (admission control).  max_slots: requests allowed
+ * on the device at once (1..64).  timeout_ms: a request not finished this
+ * long after launch reports PFB_ERR_TIMEOUT.  queue_when_busy: 1 = pfb_submit
+ * queues a request that does not fit yet; 0 = it returns PFB_ERR_BUSY. */
+typedef struct pfb_server_desc {
+    int64_t hbm_budget_bytes;
+    int32_t max_slots;
+    int32_t timeout_ms;
+    int32_t queue_when_busy;
+    int32_t device;
+} pfb_server_desc;
+
+typedef struct pfb_server_stats {
+    int64_t submitted, completed, failed, rejected;
+    int64_t queued_now, in_flight_now;
+    int64_t reserved_bytes_now, peak_reserved_bytes;
+    int64_t samples_completed;
+    double p50_latency_us, p99_latency_us, mean_latency_us; /* submit -> completion */
+} pfb_server_stats;
+
+PFB_API pfb_status pfb_server_create(const pfb_server_desc *desc, pfb_server_t *out_server);
+/* Waits (bounded by timeout_ms per request) for in-flight work, then frees. */
+PFB_API pfb_status pfb_server_destroy(pfb_server_t server);
+
+/* Open a stream: allocates its resident filter state (the last T-1 frames of
+ * input, device memory, counted against the budget).  The stream starts
+ * empty: its first chunk emits floor(n/P) - T + 1 spectra, later chunks
+ * floor(n/P) each, so the concatenated outputs equal pfb_execute on the
+ * concatenated input. */
+PFB_API pfb_status pfb_stream_open(pfb_server_t server, pfb_plan_t plan, int64_t *out_stream_id);
+PFB_API pfb_status pfb_stream_close(pfb_server_t server, int64_t stream_id);
+
+/* Spectra the next chunk of n_samples on this stream will emit, counting the
+ * chunks already submitted. */
+PFB_API int64_t pfb_stream_next_spectra(pfb_server_t server, int64_t stream_id, int64_t n_samples);
+
+/* Submit one chunk (n_samples a multiple of P, device memory) of a stream.
+ * Non-blocking: the request is admitted as soon as a slot and budget are
+ * free, runs with the stream's resident state, and chunks of one stream
+ * complete in submission order.  d_out must hold pfb_stream_next_spectra()
+ * rows.  Returns a ticket for pfb_poll/pfb_wait. */
+PFB_API pfb_status pfb_submit(pfb_server_t server, int64_t stream_id, const void *d_chunk,
+                      int64_t n_samples, void *d_out, int64_t out_cap_spectra,
+                      int64_t *out_ticket);
+
+/* PFB_PENDING while queued or running, PFB_OK once the output is complete,
+ * or the request's error.  Never blocks.  A finished ticket can be polled
+ * until pfb_server_destroy. */
+PFB_API pfb_status pfb_poll(pfb_server_t server, int64_t ticket);
+
+/* Block until the ticket finishes or timeout_ms passes (PFB_ERR_TIMEOUT). */
+PFB_API pfb_status pfb_wait(pfb_server_t server, int64_t ticket, int32_t timeout_ms);
+
+PFB_API pfb_status pfb_server_get_stats(pfb_server_t server, pfb_server_stats *out_stats);
+
+/* ---------------------------------------------------------------------- */
+/* Diagnostics                                                            */
+/* ---------------------------------------------------------------------- */
+
+PFB_API const char *pfb_status_string(pfb_status status);
+/* Message for the calling thread's most recent failed call ("" if none). */
+PFB_API const char *pfb_last_error(void);
+/* Number of kernel launches this library has issued so far (all threads). */
+PFB_API int64_t pfb_launch_count(void);
+/* Name of the kernel variant pfb_execute uses for a plan ("" for NULL). */
+PFB_API const char *pfb_plan_kernel_name(pfb_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFB_H_ */

@@ -1,0 +1,341 @@
+// Host side of the C ABI: status strings, error messages, pfb_execute,
+// pfb_execute_host and the batched entry points (work grouping, CUDA graphs).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+
+#include "internal.h"
+
+namespace pfb {
+
+std::atomic<int64_t> g_launches{0};
+static thread_local std::string t_err;
+
+void set_error(const std::string &msg) { t_err = msg; }
+void clear_error() { t_err.clear(); }
+pfb_status fail(pfb_status st, const std::string &msg) {
+    t_err = msg;
+    return st;
+}
+pfb_status cuda_fail(cudaError_t e, const char *what) {
+    t_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return PFB_ERR_CUDA;
+}
+
+int64_t generic_units(int P, int64_t S);
+int64_t fast_units(int64_t S);
+int64_t gemm_f32_units(const Plan &plan, int64_t S);
+int64_t gemm_bf16x3_units(const Plan &plan, int64_t S);
+
+int64_t family_units(const Plan &plan, int64_t S) {
+    switch (plan.family) {
+    case FAM_FFT_FAST: return fast_units(S);
+    case FAM_FFT_GENERIC: return generic_units(plan.P, S);
+    case FAM_GEMM_F32: return gemm_f32_units(plan, S);
+    case FAM_GEMM_BF16X3: return gemm_bf16x3_units(plan, S);
+    default: return 0;
+    }
+}
+
+static const float *family_taps(const Plan &plan) {
+    return plan.family == FAM_FFT_FAST ? plan.d_taps_pad : plan.d_taps;
+}
+
+// Launch the plan's family kernel over n stream descriptors (all of this
+// family/P/T/dtype), in groups of kMaxStreamsPerLaunch.
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream) {
+    for (int g0 = 0; g0 < n; g0 += kMaxStreamsPerLaunch) {
+        const int g1 = std::min(n, g0 + kMaxStreamsPerLaunch);
+        LaunchArgs a;
+        std::memset(&a, 0, sizeof(a));
+        int64_t units = 0;
+        int k = 0;
+        for (int i = g0; i < g1; ++i) {
+            if (descs[i].S <= 0) continue;
+            a.s[k] = descs[i];
+            a.s[k].unit0 = units;
+            units += family_units(plan, descs[i].S);
+            ++k;
+        }
+        if (k == 0) continue;
+        a.nstreams = k;
+        a.nunits = units;
+        a.tw = plan.d_tw;
+        a.aux = plan.d_dft;
+        a.err = plan.d_err;
+        pfb_status st;
+        switch (plan.family) {
+        case FAM_FFT_FAST: st = launch_fft_fast(plan, a, stream); break;
+        case FAM_FFT_GENERIC: st = launch_fft_generic(plan, a, stream); break;
+        case FAM_GEMM_F32: st = launch_gemm_f32(plan, a, stream); break;
+        case FAM_GEMM_BF16X3: st = launch_gemm_bf16x3(plan, a, stream); break;
+        default: st = fail(PFB_ERR_INTERNAL, "unknown kernel family");
+        }
+        if (st != PFB_OK) return st;
+    }
+    return PFB_OK;
+}
+
+// Set kernel attributes and occupancy caches for the plan's variant outside
+// any stream capture (the launchers do it on first use).
+pfb_status prepare_family(const Plan &plan) {
+    LaunchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    switch (plan.family) {
+    case FAM_FFT_FAST: return launch_fft_fast(plan, a, nullptr);
+    case FAM_FFT_GENERIC: return launch_fft_generic(plan, a, nullptr);
+    case FAM_GEMM_F32: return launch_gemm_f32(plan, a, nullptr);
+    case FAM_GEMM_BF16X3: return launch_gemm_bf16x3(plan, a, nullptr);
+    default: return PFB_OK;
+    }
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Fill a descriptor for a plain (stateless) stream; validates the arguments.
+static pfb_status make_desc(const Plan &plan, const void *d_in, int64_t n_samples, void *d_out,
+                            int64_t out_cap, StreamDesc &d) {
+    if (n_samples < 0) return fail(PFB_ERR_INVALID, "n_samples < 0");
+    const int64_t S = out_spectra(plan, n_samples);
+    std::memset(&d, 0, sizeof(d));
+    d.S = S;
+    if (S == 0) return PFB_OK;
+    if (!d_in || !d_out) return fail(PFB_ERR_INVALID, "NULL buffer with S > 0");
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(PFB_ERR_INVALID, "buffers must be 16-byte aligned");
+    if (out_cap < S) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
+    d.in = d_in;
+    d.state = nullptr;
+    d.out = static_cast<float2 *>(d_out);
+    d.n_state = 0;
+    d.n_frames = n_samples / plan.P;
+    d.taps = family_taps(plan);
+    d.scale = plan.desc.in_scale;
+    d.T = plan.T;
+    return PFB_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace pfb
+
+using namespace pfb;
+
+extern "C" const char *pfb_status_string(pfb_status s) {
+    switch (s) {
+    case PFB_OK: return "PFB_OK";
+    case PFB_PENDING: return "PFB_PENDING";
+    case PFB_ERR_INVALID: return "PFB_ERR_INVALID";
+    case PFB_ERR_OOM: return "PFB_ERR_OOM";
+    case PFB_ERR_CUDA: return "PFB_ERR_CUDA";
+    case PFB_ERR_BUSY: return "PFB_ERR_BUSY";
+    case PFB_ERR_TIMEOUT: return "PFB_ERR_TIMEOUT";
+    case PFB_ERR_INTERNAL: return "PFB_ERR_INTERNAL";
+    case PFB_ERR_UNSUPPORTED: return "PFB_ERR_UNSUPPORTED";
+    default: return "PFB_UNKNOWN_STATUS";
+    }
+}
+
+extern "C" const char *pfb_last_error(void) { return t_err.c_str(); }
+extern "C" int64_t pfb_launch_count(void) { return g_launches.load(); }
+
+extern "C" pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samples, void *d_out,
+                                  int64_t out_cap_spectra, void *cuda_stream) {
+    clear_error();
+    if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
+    const Plan &p = *reinterpret_cast<Plan *>(plan);
+    StreamDesc d;
+    pfb_status st = make_desc(p, d_in, n_samples, d_out, out_cap_spectra, d);
+    if (st != PFB_OK || d.S == 0) return st;
+    DeviceGuard g(p.device);
+    return launch_family(p, &d, 1, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples, void *host_out,
+                                       int64_t out_cap_spectra, void *cuda_stream) {
+    clear_error();
+    if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    if (n_samples < 0) return fail(PFB_ERR_INVALID, "n_samples < 0");
+    const int64_t S = out_spectra(p, n_samples);
+    if (S == 0) return PFB_OK;
+    if (!host_in || !host_out) return fail(PFB_ERR_INVALID, "NULL buffer with S > 0");
+    if (out_cap_spectra < S) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
+    const size_t in_bytes = (size_t)n_samples * p.esize;
+    const size_t out_bytes = (size_t)S * p.P * sizeof(float2);
+    std::lock_guard<std::mutex> lk(p.stage_mu);
+    DeviceGuard g(p.device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (p.stage_in_bytes < in_bytes) {
+        cudaFree(p.d_stage_in);
+        p.d_stage_in = nullptr;
+        p.stage_in_bytes = 0;
+        if (cudaMalloc(&p.d_stage_in, in_bytes) != cudaSuccess) return fail(PFB_ERR_OOM, "staging input");
+        p.stage_in_bytes = in_bytes;
+    }
+    if (p.stage_out_bytes < out_bytes) {
+        cudaFree(p.d_stage_out);
+        p.d_stage_out = nullptr;
+        p.stage_out_bytes = 0;
+        if (cudaMalloc(&p.d_stage_out, out_bytes) != cudaSuccess) return fail(PFB_ERR_OOM, "staging output");
+        p.stage_out_bytes = out_bytes;
+    }
+    PFB_CUDA_TRY(cudaMemcpyAsync(p.d_stage_in, host_in, in_bytes, cudaMemcpyHostToDevice, s));
+    StreamDesc d;
+    pfb_status st = make_desc(p, p.d_stage_in, n_samples, p.d_stage_out, S, d);
+    if (st != PFB_OK) return st;
+    st = launch_family(p, &d, 1, s);
+    if (st != PFB_OK) return st;
+    PFB_CUDA_TRY(cudaMemcpyAsync(host_out, p.d_stage_out, out_bytes, cudaMemcpyDeviceToHost, s));
+    PFB_CUDA_TRY(cudaStreamSynchronize(s));
+    return PFB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches: group streams by kernel variant, one persistent launch per group
+// ---------------------------------------------------------------------------
+namespace pfb {
+
+struct Group {
+    const Plan *plan;  // representative (P, T, dtype, family, tables of this shape)
+    std::vector<StreamDesc> descs;
+};
+
+static pfb_status build_groups(const pfb_batch_item *items, int32_t n, std::vector<Group> &groups, int &device) {
+    if (n < 0 || (n > 0 && !items)) return fail(PFB_ERR_INVALID, "bad item list");
+    std::map<std::tuple<int, int, int, int>, size_t> index;
+    device = -1;
+    for (int i = 0; i < n; ++i) {
+        const pfb_batch_item &it = items[i];
+        if (!it.plan) return fail(PFB_ERR_INVALID, "item with NULL plan");
+        const Plan &p = *reinterpret_cast<Plan *>(it.plan);
+        if (device < 0) device = p.device;
+        if (p.device != device) return fail(PFB_ERR_INVALID, "batch items span devices");
+        StreamDesc d;
+        pfb_status st = make_desc(p, it.d_in, it.n_samples, it.d_out, it.out_cap_spectra, d);
+        if (st != PFB_OK) return fail(st, "item " + std::to_string(i) + ": " + pfb_last_error());
+        if (d.S == 0) continue;
+        // streams share a launch when the kernel variant is the same; taps are
+        // per stream (descriptor), twiddles/DFT tables depend only on P
+        auto key = std::make_tuple(p.family, p.P, p.TT, p.in_dtype);
+        auto f = index.find(key);
+        if (f == index.end()) {
+            index[key] = groups.size();
+            groups.push_back(Group{&p, {}});
+            f = index.find(key);
+        }
+        groups[f->second].descs.push_back(d);
+    }
+    return PFB_OK;
+}
+
+struct Batch {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace pfb
+
+extern "C" pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_items, void *cuda_stream) {
+    clear_error();
+    std::vector<Group> groups;
+    int device = -1;
+    pfb_status st = build_groups(items, n_items, groups, device);
+    if (st != PFB_OK || groups.empty()) return st;
+    DeviceGuard g(device);
+    for (auto &gr : groups) {
+        st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), static_cast<cudaStream_t>(cuda_stream));
+        if (st != PFB_OK) return st;
+    }
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_batch_create(const pfb_batch_item *items, int32_t n_items, pfb_batch_t *out_batch) {
+    clear_error();
+    if (!out_batch) return fail(PFB_ERR_INVALID, "out_batch is NULL");
+    *out_batch = nullptr;
+    std::vector<Group> groups;
+    int device = -1;
+    pfb_status st = build_groups(items, n_items, groups, device);
+    if (st != PFB_OK) return st;
+    if (device < 0) {
+        cudaGetDevice(&device);
+    }
+    DeviceGuard g(device);
+    Batch *b = new (std::nothrow) Batch();
+    if (!b) return fail(PFB_ERR_OOM, "host allocation");
+    b->device = device;
+    // Capture every group's launch on its own forked stream so independent
+    // groups may overlap on the device; one graph, one replay.
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> side(groups.size(), nullptr);
+    std::vector<cudaEvent_t> done(groups.size(), nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (size_t i = 0; e == cudaSuccess && i < groups.size(); ++i) {
+        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, main);
+    for (size_t i = 0; e == cudaSuccess && st == PFB_OK && i < groups.size(); ++i) {
+        e = cudaStreamWaitEvent(side[i], fork, 0);
+        if (e != cudaSuccess) break;
+        st = launch_family(*groups[i].plan, groups[i].descs.data(), (int)groups[i].descs.size(), side[i]);
+        if (st == PFB_OK) e = cudaEventRecord(done[i], side[i]);
+        if (e == cudaSuccess && st == PFB_OK) e = cudaStreamWaitEvent(main, done[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(main, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && st == PFB_OK) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    b->graph = graph;
+    for (size_t i = 0; i < groups.size(); ++i) {
+        if (side[i]) cudaStreamDestroy(side[i]);
+        if (done[i]) cudaEventDestroy(done[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (main) cudaStreamDestroy(main);
+    if (st != PFB_OK || e != cudaSuccess) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return st != PFB_OK ? st : cuda_fail(e, "batch graph capture");
+    }
+    *out_batch = reinterpret_cast<pfb_batch_t>(b);
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_batch_launch(pfb_batch_t batch, void *cuda_stream) {
+    clear_error();
+    if (!batch) return fail(PFB_ERR_INVALID, "batch is NULL");
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    DeviceGuard g(b->device);
+    PFB_CUDA_TRY(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
+    g_launches++;
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_batch_destroy(pfb_batch_t batch) {
+    clear_error();
+    if (!batch) return PFB_OK;
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    DeviceGuard g(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    return PFB_OK;
+}

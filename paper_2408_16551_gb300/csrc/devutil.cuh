@@ -1,0 +1,136 @@
+// Device helpers shared by the kernels of libpfb: complex arithmetic,
+// in-register small DFTs, input loaders for the three sample types, stores.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pfb {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// b * exp(-2 pi i m / 16) for a compile-time m in [0, 8) (after unrolling the
+// switch folds away).  Constants: cos(pi/8), sin(pi/8), sqrt(1/2).
+__device__ __forceinline__ float2 twmul16(float2 b, int m) {
+    constexpr float C1 = 0.92387953251128674f;
+    constexpr float S1 = 0.38268343236508977f;
+    constexpr float H = 0.70710678118654752f;
+    switch (m) {
+    case 0: return b;
+    case 1: return cmul(b, make_float2(C1, -S1));
+    case 2: return make_float2(H * (b.x + b.y), H * (b.y - b.x));
+    case 3: return cmul(b, make_float2(S1, -C1));
+    case 4: return make_float2(b.y, -b.x);
+    case 5: return cmul(b, make_float2(-S1, -C1));
+    case 6: return make_float2(H * (b.y - b.x), -H * (b.x + b.y));
+    default: return cmul(b, make_float2(-C1, -S1));
+    }
+}
+
+template <int R>
+__device__ __forceinline__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) {
+        r = (r << 1) | (i & 1);
+        i >>= 1;
+    }
+    return r;
+}
+
+// In-register forward DFT, natural order in and out:
+//   v[k] <- sum_r v[r] exp(-2 pi i r k / R),  R in {2, 4, 8, 16}
+// (iterative radix-2 decimation in time over a bit-reversed copy).
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+    float2 t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) t[i] = v[bitrev<R>(i)];
+#pragma unroll
+    for (int len = 2; len <= R; len <<= 1) {
+#pragma unroll
+        for (int i = 0; i < R; i += len) {
+#pragma unroll
+            for (int k = 0; k < len / 2; ++k) {
+                float2 a = t[i + k];
+                float2 b = twmul16(t[i + k + len / 2], (16 / len) * k);
+                t[i + k] = cadd(a, b);
+                t[i + k + len / 2] = csub(a, b);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// ---------------------------------------------------------------------------
+// input loaders: two consecutive branches (samples idx, idx+1) as complex fp32
+// ---------------------------------------------------------------------------
+template <int IN>
+struct Loader;
+
+template <>
+struct Loader<PFB_IN_C64> {
+    static constexpr bool kReal = false;
+    __device__ __forceinline__ static void load2(const void *base, int64_t idx, float, float2 &a, float2 &b) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(static_cast<const float2 *>(base) + idx));
+        a = make_float2(v.x, v.y);
+        b = make_float2(v.z, v.w);
+    }
+    __device__ __forceinline__ static float2 load1(const void *base, int64_t idx, float) {
+        return __ldg(static_cast<const float2 *>(base) + idx);
+    }
+};
+
+template <>
+struct Loader<PFB_IN_R32> {
+    static constexpr bool kReal = true;
+    __device__ __forceinline__ static void load2(const void *base, int64_t idx, float, float2 &a, float2 &b) {
+        float2 v = __ldg(reinterpret_cast<const float2 *>(static_cast<const float *>(base) + idx));
+        a = make_float2(v.x, 0.f);
+        b = make_float2(v.y, 0.f);
+    }
+    __device__ __forceinline__ static float2 load1(const void *base, int64_t idx, float) {
+        return make_float2(__ldg(static_cast<const float *>(base) + idx), 0.f);
+    }
+};
+
+template <>
+struct Loader<PFB_IN_CI8> {
+    static constexpr bool kReal = false;
+    __device__ __forceinline__ static void load2(const void *base, int64_t idx, float s, float2 &a, float2 &b) {
+        char4 v = __ldg(reinterpret_cast<const char4 *>(static_cast<const int8_t *>(base) + 2 * idx));
+        a = make_float2((float)v.x * s, (float)v.y * s);
+        b = make_float2((float)v.z * s, (float)v.w * s);
+    }
+    __device__ __forceinline__ static float2 load1(const void *base, int64_t idx, float s) {
+        char2 v = __ldg(reinterpret_cast<const char2 *>(static_cast<const int8_t *>(base) + 2 * idx));
+        return make_float2((float)v.x * s, (float)v.y * s);
+    }
+};
+
+// frame f of a stream: the state frames come first, then the input frames
+__device__ __forceinline__ const void *frame_source(const StreamDesc &d, int64_t f, int64_t P, int64_t &sample) {
+    if (f < d.n_state) {
+        sample = f * P;
+        return d.state;
+    }
+    sample = (f - d.n_state) * P;
+    return d.in;
+}
+
+__device__ __forceinline__ void store_cs(float2 *p, float2 v) { __stcs(p, v); }
+
+// locate the stream owning global work unit u (streams sorted by unit0)
+__device__ __forceinline__ int find_stream(const LaunchArgs &a, int64_t u) {
+    int i = 0;
+    while (i + 1 < a.nstreams && a.s[i + 1].unit0 <= u) ++i;
+    return i;
+}
+
+}  // namespace pfb

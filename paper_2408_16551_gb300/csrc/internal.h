@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of libpfb.
+// Not part of the public ABI (include/pfb.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pfb.h"
+
+namespace pfb {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+void clear_error();
+pfb_status fail(pfb_status st, const std::string &msg);
+pfb_status cuda_fail(cudaError_t e, const char *what);
+extern std::atomic<int64_t> g_launches;
+
+#define PFB_CUDA_TRY(expr)                                           \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) return ::pfb::cuda_fail(_e, #expr);   \
+    } while (0)
+
+// Device-side error word values (written by kernels, read by the host).
+enum : int {
+    KERR_NONE = 0,
+    KERR_BOUNDS = 1,     // a work index fell outside its descriptor table
+    KERR_TIMEOUT = 2,    // a bounded device-side wait ran out
+    KERR_CONFIG = 3,     // kernel launched with a configuration it does not support
+};
+
+// ---------------------------------------------------------------------------
+// per-stream work descriptor (one stream = one contiguous run of frames)
+//
+// The frames of a stream are the n_state frames of `state` followed by the
+// frames of `in`; spectra s = 0 .. S-1 use frames s .. s+T-1 of that sequence.
+// ---------------------------------------------------------------------------
+struct StreamDesc {
+    const void *in;        // input samples (raw dtype)
+    const void *state;     // resident state frames (raw dtype) or nullptr
+    float2 *out;           // output spectra [S][P] complex64
+    int64_t n_state;       // frames taken from `state` (precede `in`)
+    int64_t n_frames;      // total frames available (state + in)
+    int64_t S;             // spectra to produce
+    int64_t unit0;         // index of this stream's first work unit in the launch
+    const float *taps;     // fp32 taps, layout depends on the kernel family
+    float scale;           // dequantisation factor (CI8)
+    int32_t T;             // taps per branch
+};
+
+constexpr int kMaxStreamsPerLaunch = 32;
+
+struct LaunchArgs {
+    StreamDesc s[kMaxStreamsPerLaunch];
+    int32_t nstreams;
+    int32_t units_per_cta;  // contiguous work units per CTA (persistent ranges)
+    int64_t nunits;         // total work units in this launch
+    const float2 *tw;       // FFT twiddle table for the family's P
+    const void *aux;        // family-specific table (DFT matrix for GEMM paths)
+    int *err;               // device error word
+};
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+enum KernelFamily : int {
+    FAM_FFT_FAST = 0,     // fused FIR + radix-16 Stockham FFT, P in [64,1024], T <= 16
+    FAM_FFT_GENERIC = 1,  // fused FIR + radix-2 Stockham FFT, any supported P, T
+    FAM_GEMM_F32 = 2,     // fused FIR + DFT-matrix product, FP32 SIMT
+    FAM_GEMM_BF16X3 = 3,  // fused FIR + DFT-matrix product, tcgen05 split-bf16
+};
+
+struct Plan {
+    pfb_plan_desc desc;
+    int device = 0;
+    int P = 0, T = 0, TT = 0;       // TT: tap count the kernel is compiled for (>= T)
+    int in_dtype = 0;
+    int path = 0;
+    int family = 0;
+    int esize = 0;                  // bytes per input sample
+    // device tables (owned)
+    double *d_h64 = nullptr;        // FP64 prototype [P*T]
+    float *d_taps = nullptr;        // fp32 taps [T][P]
+    float *d_taps_pad = nullptr;    // fp32 taps front-padded [TT][P] (fast FFT family)
+    float2 *d_tw = nullptr;         // FFT twiddles (layout per family)
+    float2 *d_tw_r2 = nullptr;      // radix-2 table w^r, r < P/2 (generic family)
+    void *d_dft = nullptr;          // DFT matrix (GEMM families)
+    size_t dft_bytes = 0;
+    int *d_err = nullptr;           // device error word
+    // host staging for pfb_execute_host
+    std::mutex stage_mu;
+    void *d_stage_in = nullptr, *d_stage_out = nullptr;
+    size_t stage_in_bytes = 0, stage_out_bytes = 0;
+    std::string kernel_name;
+};
+
+int64_t out_spectra(const Plan &p, int64_t n_samples);
+bool is_pow2(int64_t v);
+int ilog2(int64_t v);
+
+// Launch one kernel of the plan's family over the given streams (all with
+// the plan's P, T, dtype).  `descs` unit0 fields are filled in here.
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream);
+
+// Family-specific launchers (defined in their .cu files).
+pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status launch_fft_generic(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status prepare_family(const Plan &plan);
+// work units a stream of S spectra contributes to a launch of the plan's family
+int64_t family_units(const Plan &plan, int64_t S);
+bool fft_fast_supported(int P, int T);
+int fft_fast_tt(int T);
+
+// Table generators (plan.cu)
+pfb_status build_fft_fast_twiddles(Plan &plan);
+pfb_status build_gemm_tables(Plan &plan);
+
+// stream-state update for serving: new_state = last n_keep frames of (state ++ chunk)
+pfb_status launch_state_update(const void *old_state, int64_t old_frames, const void *chunk,
+                               int64_t chunk_frames, void *new_state, int64_t n_keep,
+                               int64_t frame_bytes, cudaStream_t stream);
+
+}  // namespace pfb

@@ -1,0 +1,273 @@
+// Plan creation: validation, FP64 table generation on the GPU, plan lifetime.
+//
+// Everything here runs once per plan.  FP64 is used on the GPU only in these
+// generators: the windowed-sinc prototype (the branch taps of Sec. 5.2), the
+// FFT twiddles and the DFT matrix (the Fourier matrix of Sec. 4.1).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fftplan.h"
+#include "internal.h"
+
+namespace pfb {
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << r) < v) ++r;
+    return r;
+}
+
+int64_t out_spectra(const Plan &p, int64_t n_samples) {
+    if (n_samples < 0) return -1;
+    int64_t F = n_samples / p.P;
+    int64_t S = F - p.T + 1;
+    return S > 0 ? S : 0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 generators
+// ---------------------------------------------------------------------------
+
+// Symmetric window over L points times sinc((n-c)/P), c = (L-1)/2.
+__global__ void gen_prototype_kernel(double *h, int P, int L, int window) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L) return;
+    double w = 1.0;
+    if (L > 1) {
+        double a = 2.0 * (double)n / (double)(L - 1);  // angle / pi
+        switch (window) {
+        case PFB_WIN_HANN: w = 0.5 - 0.5 * cospi(a); break;
+        case PFB_WIN_HAMMING: w = 0.54 - 0.46 * cospi(a); break;
+        case PFB_WIN_BLACKMAN: w = 0.42 - 0.5 * cospi(a) + 0.08 * cospi(2.0 * a); break;
+        default: break;
+        }
+    }
+    double u = ((double)n - 0.5 * (double)(L - 1)) / (double)P;
+    double s = (u == 0.0) ? 1.0 : sinpi(u) / (3.14159265358979323846 * u);
+    h[n] = w * s;
+}
+
+// One block: deterministic FP64 sum, then h /= sum.
+__global__ void normalise_kernel(double *h, int L) {
+    __shared__ double part[1024];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) acc += h[i];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    double sum = part[0];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) h[i] = h[i] / sum;
+}
+
+// taps[m][p] = h[m*P+p] (fp32) and the zero-extended copy used by the fast
+// FFT family: pad[m][p] = h[m*P+p] for m < T, 0 for T <= m < TT.
+__global__ void taps_to_f32_kernel(const double *h, int P, int T, int TT, float *taps, float *pad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P * T) taps[i] = (float)h[i];
+    if (pad && i < P * TT) pad[i] = (i < P * T) ? (float)h[i] : 0.0f;
+}
+
+// exp(-2 pi i e / M) in FP64, rounded to fp32.
+__device__ __forceinline__ float2 twiddle64(int64_t e, int64_t M) {
+    e %= M;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)M, &s, &c);
+    return make_float2((float)c, (float)-s);
+}
+
+// radix-2 table: w^r = exp(-2 pi i r / P), r < P/2
+__global__ void gen_tw_r2_kernel(float2 *tw, int P) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < P / 2) tw[r] = twiddle64(r, P);
+}
+
+// Stockham pass tables of the fast FFT family: for each pass (Ns, R) with
+// Ns > 1, entries [(j mod Ns)*(R-1) + r-1] = exp(-2 pi i r j / (Ns R)).
+__global__ void gen_tw_pass_kernel(float2 *tw, int Ns, int R) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ns * (R - 1)) return;
+    int j = i / (R - 1), r = i % (R - 1) + 1;
+    tw[i] = twiddle64((int64_t)r * j, (int64_t)Ns * R);
+}
+
+// ---------------------------------------------------------------------------
+// fast-FFT family twiddles (pass list in fftplan.h)
+// ---------------------------------------------------------------------------
+pfb_status build_fft_fast_twiddles(Plan &plan) {
+    const int P = plan.P;
+    int total = fft_tw_entries(P);
+    PFB_CUDA_TRY(cudaMalloc(&plan.d_tw, (total > 0 ? total : 1) * sizeof(float2)));
+    for (int i = 0; i < fft_npasses(P); ++i) {
+        int Ns = fft_ns(P, i), R = fft_radix(P, i);
+        if (Ns == 1) continue;
+        int n = Ns * (R - 1);
+        gen_tw_pass_kernel<<<(n + 255) / 256, 256>>>(plan.d_tw + fft_tw_offset(P, i), Ns, R);
+        g_launches++;
+    }
+    PFB_CUDA_TRY(cudaGetLastError());
+    return PFB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan lifetime
+// ---------------------------------------------------------------------------
+
+static pfb_status validate(const pfb_plan_desc *d) {
+    if (!d) return fail(PFB_ERR_INVALID, "descriptor is NULL");
+    if (!is_pow2(d->P) || d->P < 4 || d->P > 4096)
+        return fail(PFB_ERR_INVALID, "P must be a power of two in [4, 4096]");
+    if (d->T < 1 || d->T > 64) return fail(PFB_ERR_INVALID, "T must be in [1, 64]");
+    if (d->in_dtype < PFB_IN_R32 || d->in_dtype > PFB_IN_CI8) return fail(PFB_ERR_INVALID, "bad in_dtype");
+    if (d->window < PFB_WIN_HANN || d->window > PFB_WIN_USER) return fail(PFB_ERR_INVALID, "bad window");
+    if (d->window == PFB_WIN_USER && !d->user_taps_host)
+        return fail(PFB_ERR_INVALID, "window USER needs user_taps_host");
+    if (d->window != PFB_WIN_USER && d->user_taps_host)
+        return fail(PFB_ERR_INVALID, "user_taps_host given without window USER");
+    if (d->path < PFB_DFT_FFT_F32 || d->path > PFB_DFT_GEMM_BF16X3) return fail(PFB_ERR_INVALID, "bad path");
+    if (d->in_dtype == PFB_IN_CI8 && !std::isfinite(d->in_scale))
+        return fail(PFB_ERR_INVALID, "in_scale must be finite");
+    if (d->reserved != 0) return fail(PFB_ERR_INVALID, "reserved field must be 0");
+    return PFB_OK;
+}
+
+static void free_plan(Plan *p) {
+    if (!p) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaFree(p->d_h64);
+    cudaFree(p->d_taps);
+    cudaFree(p->d_taps_pad);
+    cudaFree(p->d_tw);
+    cudaFree(p->d_tw_r2);
+    cudaFree(p->d_dft);
+    cudaFree(p->d_err);
+    cudaFree(p->d_stage_in);
+    cudaFree(p->d_stage_out);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete p;
+}
+
+static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
+    p->desc = *desc;
+    p->desc.user_taps_host = nullptr;
+    p->P = desc->P;
+    p->T = desc->T;
+    p->in_dtype = desc->in_dtype;
+    p->path = desc->path;
+    p->esize = desc->in_dtype == PFB_IN_R32 ? 4 : desc->in_dtype == PFB_IN_C64 ? 8 : 2;
+    if (desc->path == PFB_DFT_FFT_F32) {
+        p->family = fft_fast_supported(p->P, p->T) ? FAM_FFT_FAST : FAM_FFT_GENERIC;
+    } else if (desc->path == PFB_DFT_GEMM_F32) {
+        p->family = FAM_GEMM_F32;
+    } else {
+        p->family = FAM_GEMM_BF16X3;
+    }
+    p->TT = (p->family == FAM_FFT_FAST) ? fft_fast_tt(p->T) : p->T;
+
+    const int P = p->P, T = p->T, L = P * T;
+    PFB_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
+    PFB_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+    PFB_CUDA_TRY(cudaMalloc(&p->d_h64, sizeof(double) * L));
+    if (desc->window == PFB_WIN_USER) {
+        PFB_CUDA_TRY(cudaMemcpy(p->d_h64, desc->user_taps_host, sizeof(double) * L, cudaMemcpyHostToDevice));
+    } else {
+        gen_prototype_kernel<<<(L + 255) / 256, 256>>>(p->d_h64, P, L, desc->window);
+        normalise_kernel<<<1, 1024>>>(p->d_h64, L);
+        g_launches += 2;
+    }
+    PFB_CUDA_TRY(cudaMalloc(&p->d_taps, sizeof(float) * L));
+    if (p->family == FAM_FFT_FAST) PFB_CUDA_TRY(cudaMalloc(&p->d_taps_pad, sizeof(float) * P * p->TT));
+    int nconv = P * (p->TT > T ? p->TT : T);
+    taps_to_f32_kernel<<<(nconv + 255) / 256, 256>>>(p->d_h64, P, T, p->TT, p->d_taps, p->d_taps_pad);
+    g_launches++;
+
+    PFB_CUDA_TRY(cudaMalloc(&p->d_tw_r2, sizeof(float2) * (P / 2)));
+    gen_tw_r2_kernel<<<(P / 2 + 255) / 256, 256>>>(p->d_tw_r2, P);
+    g_launches++;
+    if (p->family == FAM_FFT_FAST) {
+        pfb_status st = build_fft_fast_twiddles(*p);
+        if (st != PFB_OK) return st;
+    }
+    if (p->family == FAM_GEMM_F32 || p->family == FAM_GEMM_BF16X3) {
+        pfb_status st = build_gemm_tables(*p);
+        if (st != PFB_OK) return st;
+    }
+    PFB_CUDA_TRY(cudaGetLastError());
+    PFB_CUDA_TRY(cudaDeviceSynchronize());
+    if (p->family != FAM_GEMM_F32 && p->family != FAM_GEMM_BF16X3) {
+        pfb_status pst = prepare_family(*p);
+        if (pst != PFB_OK) return pst;
+    }
+    static const char *fam_names[] = {"pfb_fir_fft_f32", "pfb_fir_fft_f32_generic",
+                                      "pfb_fir_dftgemm_f32", "pfb_fir_dftgemm_bf16x3"};
+    p->kernel_name = fam_names[p->family];
+    return PFB_OK;
+}
+
+}  // namespace pfb
+
+using namespace pfb;
+
+extern "C" pfb_status pfb_plan_create(const pfb_plan_desc *desc, pfb_plan_t *out_plan) {
+    clear_error();
+    if (!out_plan) return fail(PFB_ERR_INVALID, "out_plan is NULL");
+    *out_plan = nullptr;
+    pfb_status st = validate(desc);
+    if (st != PFB_OK) return st;
+    int dev = desc->device;
+    int ndev = 0;
+    PFB_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    int prev = 0;
+    PFB_CUDA_TRY(cudaGetDevice(&prev));
+    if (dev < 0) dev = prev;
+    if (dev >= ndev) return fail(PFB_ERR_INVALID, "device ordinal out of range");
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return fail(PFB_ERR_OOM, "host allocation failed");
+    p->device = dev;
+    cudaSetDevice(dev);
+    st = create_impl(desc, p);
+    cudaSetDevice(prev);
+    if (st != PFB_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out_plan = reinterpret_cast<pfb_plan_t>(p);
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_plan_destroy(pfb_plan_t plan) {
+    clear_error();
+    free_plan(reinterpret_cast<Plan *>(plan));
+    return PFB_OK;
+}
+
+extern "C" int64_t pfb_out_spectra(pfb_plan_t plan, int64_t n_samples) {
+    if (!plan || n_samples < 0) return -1;
+    return out_spectra(*reinterpret_cast<Plan *>(plan), n_samples);
+}
+
+extern "C" pfb_status pfb_plan_get_taps(pfb_plan_t plan, double *host_out, int64_t cap) {
+    clear_error();
+    if (!plan || !host_out) return fail(PFB_ERR_INVALID, "NULL argument");
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    int64_t L = (int64_t)p->P * p->T;
+    if (cap < L) return fail(PFB_ERR_INVALID, "cap < P*T");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaError_t e = cudaMemcpy(host_out, p->d_h64, sizeof(double) * L, cudaMemcpyDeviceToHost);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy taps");
+    return PFB_OK;
+}
+
+extern "C" const char *pfb_plan_kernel_name(pfb_plan_t plan) {
+    if (!plan) return "";
+    return reinterpret_cast<Plan *>(plan)->kernel_name.c_str();
+}

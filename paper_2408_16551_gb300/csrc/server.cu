@@ -1,0 +1,527 @@
+// Serving: continuous batching of channelisation requests.
+//
+// A request is one chunk of one stream.  Each stream keeps its filter state on
+// the device -- the last T-1 frames of raw input -- so that chunk c sees
+// state ++ chunk as its frame sequence and the concatenated outputs equal the
+// single-pass channeliser on the concatenated input (spectra are the "valid"
+// outputs of Sec. 5.2's per-branch FIR).  State lives in two device buffers
+// per stream (read one, write the other), so consecutive chunks of a stream
+// can be queued back to back on the stream's CUDA stream without host waits.
+//
+// Admission: requests are taken in submission order; one is launched when
+// fewer than max_slots requests are on the device and the bytes it pins (its
+// input and output buffers) fit in the HBM budget next to the resident state
+// of all open streams.  Requests of different streams run on different CUDA
+// streams of a pool and overlap on the device.  A host scheduler thread
+// admits queued requests and observes completions (cudaEventQuery every few
+// microseconds while work is in flight); latency is submit -> observed
+// completion.  A request whose completion is not seen within timeout_ms
+// reports PFB_ERR_TIMEOUT; its slot stays held until the device finishes it.
+//
+// Host-side fault injection for tests (no GPU fault is ever provoked):
+//   PFB_FAULT=launch_fail:<k>   the k-th launch attempt (1-based) is not issued
+//                               and its request fails with PFB_ERR_CUDA;
+//   PFB_FAULT=lose_completion:<k>  the k-th launched request's completion is
+//                               never observed, so it times out.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <thread>
+
+#include "internal.h"
+
+namespace pfb {
+
+using Clock = std::chrono::steady_clock;
+
+// new_state[i] = frame (old_frames + chunk_frames - n_keep + i) of (state ++ chunk)
+__global__ void k_state_update(const uint2 *old_state, int64_t old_frames, const uint2 *chunk, int64_t chunk_frames,
+                               uint2 *new_state, int64_t n_keep, int64_t words_per_frame) {
+    const int64_t total = n_keep * words_per_frame;
+    const int64_t first = old_frames + chunk_frames - n_keep;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = w / words_per_frame, off = w - i * words_per_frame;
+        const int64_t g = first + i;
+        new_state[w] = (g < old_frames) ? old_state[g * words_per_frame + off]
+                                        : chunk[(g - old_frames) * words_per_frame + off];
+    }
+}
+
+pfb_status launch_state_update(const void *old_state, int64_t old_frames, const void *chunk, int64_t chunk_frames,
+                               void *new_state, int64_t n_keep, int64_t frame_bytes, cudaStream_t stream) {
+    if (n_keep <= 0) return PFB_OK;
+    const int64_t wpf = frame_bytes / 8;
+    const int64_t total = n_keep * wpf;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 1024);
+    k_state_update<<<blocks, threads, 0, stream>>>(static_cast<const uint2 *>(old_state), old_frames,
+                                                   static_cast<const uint2 *>(chunk), chunk_frames,
+                                                   static_cast<uint2 *>(new_state), n_keep, wpf);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_state_update");
+    return PFB_OK;
+}
+
+struct Request {
+    int64_t ticket = 0, stream_id = 0;
+    const void *d_chunk = nullptr;
+    void *d_out = nullptr;
+    int64_t n_samples = 0, S = 0, bytes = 0;
+    pfb_status status = PFB_PENDING;
+    bool launched = false, lost = false;
+    int pool_index = 0;
+    cudaEvent_t done = nullptr;
+    Clock::time_point t_submit, t_launch, t_done;
+};
+
+struct PStream {
+    int64_t id = 0;
+    Plan *plan = nullptr;
+    void *state[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t state_frames = 0;       // valid frames in state[cur] at the next launch
+    int64_t frames_submitted = 0;   // frames of all chunks submitted so far
+    int64_t state_bytes = 0;
+    int64_t outstanding = 0;        // submitted and not finished
+    int pool_index = 0;
+    bool closing = false;
+};
+
+struct Server {
+    pfb_server_desc desc;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    std::vector<cudaStream_t> pool;
+    std::map<int64_t, std::unique_ptr<PStream>> streams;
+    std::map<int64_t, std::unique_ptr<Request>> tickets;
+    std::deque<Request *> queue;      // submitted, not launched (submission order)
+    std::vector<Request *> inflight;  // launched, completion not observed
+    int64_t next_stream = 1, next_ticket = 1;
+    int64_t reserved = 0, peak_reserved = 0;
+    int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_rejected = 0, samples_completed = 0;
+    std::vector<double> latencies_us;
+    int64_t launch_attempts = 0, launches_done = 0;
+    int64_t fault_launch_fail = -1, fault_lose = -1;
+};
+
+static void parse_faults(Server &s) {
+    const char *f = std::getenv("PFB_FAULT");
+    if (!f) return;
+    std::string v(f);
+    auto num = [&](const std::string &key) -> int64_t {
+        size_t p = v.find(key + ":");
+        if (p == std::string::npos) return -1;
+        return std::atoll(v.c_str() + p + key.size() + 1);
+    };
+    s.fault_launch_fail = num("launch_fail");
+    s.fault_lose = num("lose_completion");
+}
+
+// Launch one request (mutex held).  Returns the request's status.
+static pfb_status launch_request(Server &s, Request &r) {
+    PStream &ps = *s.streams.at(r.stream_id);
+    Plan &plan = *ps.plan;
+    cudaStream_t cs = s.pool[ps.pool_index];
+    r.pool_index = ps.pool_index;
+    r.t_launch = Clock::now();
+    s.launch_attempts++;
+    if (s.launch_attempts == s.fault_launch_fail) return fail(PFB_ERR_CUDA, "injected launch failure");
+    const int64_t F = r.n_samples / plan.P;
+    const int64_t n_frames = ps.state_frames + F;
+    if (r.S > 0) {
+        StreamDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.in = r.d_chunk;
+        d.state = ps.state[ps.cur];
+        d.out = static_cast<float2 *>(r.d_out);
+        d.n_state = ps.state_frames;
+        d.n_frames = n_frames;
+        d.S = r.S;
+        d.taps = plan.family == FAM_FFT_FAST ? plan.d_taps_pad : plan.d_taps;
+        d.scale = plan.desc.in_scale;
+        d.T = plan.T;
+        pfb_status st = launch_family(plan, &d, 1, cs);
+        if (st != PFB_OK) return st;
+    }
+    const int64_t keep = std::min<int64_t>(plan.T - 1, n_frames);
+    pfb_status st = launch_state_update(ps.state[ps.cur], ps.state_frames, r.d_chunk, F, ps.state[ps.cur ^ 1], keep,
+                                        (int64_t)plan.P * plan.esize, cs);
+    if (st != PFB_OK) return st;
+    ps.cur ^= 1;
+    ps.state_frames = keep;
+    cudaError_t e = cudaEventRecord(r.done, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    r.launched = true;
+    s.launches_done++;
+    if (s.launches_done == s.fault_lose) r.lost = true;
+    return PFB_OK;
+}
+
+static void finish(Server &s, Request &r, pfb_status st) {
+    r.status = st;
+    r.t_done = Clock::now();
+    PStream &ps = *s.streams.at(r.stream_id);
+    ps.outstanding--;
+    if (st == PFB_OK) {
+        s.n_completed++;
+        s.samples_completed += r.n_samples;
+        s.latencies_us.push_back(std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count());
+    } else {
+        s.n_failed++;
+    }
+}
+
+// Admit queued requests in submission order while slots and budget allow.
+static void admit(Server &s) {
+    while (!s.queue.empty()) {
+        Request *r = s.queue.front();
+        if ((int64_t)s.inflight.size() >= s.desc.max_slots) return;
+        if (s.reserved + r->bytes > s.desc.hbm_budget_bytes) return;
+        s.queue.pop_front();
+        pfb_status st = launch_request(s, *r);
+        if (st == PFB_OK) {
+            s.reserved += r->bytes;
+            s.peak_reserved = std::max(s.peak_reserved, s.reserved);
+            s.inflight.push_back(r);
+        } else {
+            finish(s, *r, st);
+        }
+    }
+}
+
+static void poll_inflight(Server &s) {
+    const auto now = Clock::now();
+    for (size_t i = 0; i < s.inflight.size();) {
+        Request *r = s.inflight[i];
+        cudaError_t q = r->lost ? cudaErrorNotReady : cudaEventQuery(r->done);
+        bool device_done = (q == cudaSuccess);
+        if (q != cudaSuccess && q != cudaErrorNotReady) {
+            cudaGetLastError();
+            device_done = true;
+        }
+        if (r->status == PFB_PENDING) {
+            if (device_done) {
+                finish(s, *r, q == cudaSuccess ? PFB_OK : PFB_ERR_CUDA);
+            } else if (std::chrono::duration<double, std::milli>(now - r->t_launch).count() > s.desc.timeout_ms) {
+                finish(s, *r, PFB_ERR_TIMEOUT);
+            }
+        }
+        // the slot and the budget are released only once the device is done
+        // (a timed-out request whose completion is lost keeps holding them)
+        if (device_done && !r->lost) {
+            s.reserved -= r->bytes;
+            s.inflight[i] = s.inflight.back();
+            s.inflight.pop_back();
+        } else {
+            ++i;
+        }
+    }
+}
+
+static void worker_loop(Server *sp) {
+    Server &s = *sp;
+    cudaSetDevice(s.device);
+    std::unique_lock<std::mutex> lk(s.mu);
+    while (!s.stop) {
+        if (s.inflight.empty() && s.queue.empty()) {
+            s.cv_work.wait(lk, [&] { return s.stop || !s.inflight.empty() || !s.queue.empty(); });
+            continue;
+        }
+        size_t before = s.n_completed + s.n_failed;
+        poll_inflight(s);
+        admit(s);
+        if ((size_t)(s.n_completed + s.n_failed) != before) s.cv_done.notify_all();
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(5));
+        lk.lock();
+    }
+}
+
+}  // namespace pfb
+
+using namespace pfb;
+
+extern "C" pfb_status pfb_server_create(const pfb_server_desc *desc, pfb_server_t *out_server) {
+    clear_error();
+    if (!out_server) return fail(PFB_ERR_INVALID, "out_server is NULL");
+    *out_server = nullptr;
+    if (!desc) return fail(PFB_ERR_INVALID, "desc is NULL");
+    if (desc->hbm_budget_bytes <= 0) return fail(PFB_ERR_INVALID, "hbm_budget_bytes must be > 0");
+    if (desc->max_slots < 1 || desc->max_slots > 64) return fail(PFB_ERR_INVALID, "max_slots must be in [1, 64]");
+    if (desc->timeout_ms < 1) return fail(PFB_ERR_INVALID, "timeout_ms must be >= 1");
+    if (desc->queue_when_busy != 0 && desc->queue_when_busy != 1) return fail(PFB_ERR_INVALID, "queue_when_busy must be 0 or 1");
+    int ndev = 0;
+    PFB_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    int dev = desc->device;
+    if (dev < 0) PFB_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= ndev) return fail(PFB_ERR_INVALID, "device ordinal out of range");
+    Server *s = new (std::nothrow) Server();
+    if (!s) return fail(PFB_ERR_OOM, "host allocation");
+    s->desc = *desc;
+    s->device = dev;
+    parse_faults(*s);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(dev);
+    const int npool = std::min(desc->max_slots, 16);
+    for (int i = 0; i < npool; ++i) {
+        cudaStream_t cs;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (auto p : s->pool) cudaStreamDestroy(p);
+            cudaSetDevice(prev);
+            delete s;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        s->pool.push_back(cs);
+    }
+    cudaSetDevice(prev);
+    s->worker = std::thread(worker_loop, s);
+    *out_server = reinterpret_cast<pfb_server_t>(s);
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_server_destroy(pfb_server_t server) {
+    clear_error();
+    if (!server) return PFB_OK;
+    Server *s = reinterpret_cast<Server *>(server);
+    pfb_status result = PFB_OK;
+    {
+        // bounded wait for queued and in-flight work
+        std::unique_lock<std::mutex> lk(s->mu);
+        const auto limit = Clock::now() + std::chrono::milliseconds((int64_t)s->desc.timeout_ms * 2 + 100);
+        while ((!s->inflight.empty() || !s->queue.empty()) && Clock::now() < limit) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+            lk.lock();
+        }
+        if (!s->inflight.empty() || !s->queue.empty()) result = fail(PFB_ERR_TIMEOUT, "work still in flight at destroy");
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->worker.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    for (auto cs : s->pool) cudaStreamSynchronize(cs);
+    for (auto &kv : s->tickets)
+        if (kv.second->done) cudaEventDestroy(kv.second->done);
+    for (auto &kv : s->streams) {
+        cudaFree(kv.second->state[0]);
+        cudaFree(kv.second->state[1]);
+    }
+    for (auto cs : s->pool) cudaStreamDestroy(cs);
+    cudaSetDevice(prev);
+    delete s;
+    return result;
+}
+
+extern "C" pfb_status pfb_stream_open(pfb_server_t server, pfb_plan_t plan, int64_t *out_stream_id) {
+    clear_error();
+    if (!server || !plan || !out_stream_id) return fail(PFB_ERR_INVALID, "NULL argument");
+    Server &s = *reinterpret_cast<Server *>(server);
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (p->device != s.device) return fail(PFB_ERR_INVALID, "plan is on another device");
+    const int64_t bytes = (int64_t)std::max(p->T - 1, 1) * p->P * p->esize;
+    std::lock_guard<std::mutex> lk(s.mu);
+    if (s.reserved + 2 * bytes > s.desc.hbm_budget_bytes) return fail(PFB_ERR_OOM, "stream state does not fit the budget");
+    auto ps = std::make_unique<PStream>();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s.device);
+    cudaError_t e = cudaMalloc(&ps->state[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ps->state[1], bytes);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaFree(ps->state[0]);
+        cudaFree(ps->state[1]);
+        return fail(PFB_ERR_OOM, "stream state allocation");
+    }
+    ps->id = s.next_stream++;
+    ps->plan = p;
+    ps->state_bytes = 2 * bytes;
+    ps->pool_index = (int)(ps->id % (int64_t)s.pool.size());
+    s.reserved += ps->state_bytes;
+    s.peak_reserved = std::max(s.peak_reserved, s.reserved);
+    *out_stream_id = ps->id;
+    s.streams[ps->id] = std::move(ps);
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_stream_close(pfb_server_t server, int64_t stream_id) {
+    clear_error();
+    if (!server) return fail(PFB_ERR_INVALID, "server is NULL");
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::unique_lock<std::mutex> lk(s.mu);
+    auto it = s.streams.find(stream_id);
+    if (it == s.streams.end() || it->second->closing) return fail(PFB_ERR_INVALID, "unknown stream");
+    PStream &ps = *it->second;
+    ps.closing = true;
+    const auto limit = Clock::now() + std::chrono::milliseconds((int64_t)s.desc.timeout_ms * 2 + 100);
+    while (ps.outstanding > 0 && Clock::now() < limit) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+        lk.lock();
+    }
+    if (ps.outstanding > 0) return fail(PFB_ERR_TIMEOUT, "stream still has work in flight");
+    // wait until no in-flight request of this stream can still read the state
+    bool busy = true;
+    while (busy && Clock::now() < limit) {
+        busy = false;
+        for (Request *r : s.inflight)
+            if (r->stream_id == stream_id) busy = true;
+        if (busy) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+            lk.lock();
+        }
+    }
+    if (busy) return fail(PFB_ERR_TIMEOUT, "stream state still in use");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s.device);
+    cudaStreamSynchronize(s.pool[ps.pool_index]);
+    cudaFree(ps.state[0]);
+    cudaFree(ps.state[1]);
+    cudaSetDevice(prev);
+    s.reserved -= ps.state_bytes;
+    s.streams.erase(it);
+    return PFB_OK;
+}
+
+static int64_t next_spectra_locked(const PStream &ps, int64_t n_samples) {
+    const int64_t T = ps.plan->T;
+    const int64_t st = std::min<int64_t>(T - 1, ps.frames_submitted);
+    const int64_t S = st + n_samples / ps.plan->P - T + 1;
+    return S > 0 ? S : 0;
+}
+
+extern "C" int64_t pfb_stream_next_spectra(pfb_server_t server, int64_t stream_id, int64_t n_samples) {
+    if (!server || n_samples < 0) return -1;
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.streams.find(stream_id);
+    if (it == s.streams.end()) return -1;
+    return next_spectra_locked(*it->second, n_samples);
+}
+
+extern "C" pfb_status pfb_submit(pfb_server_t server, int64_t stream_id, const void *d_chunk, int64_t n_samples,
+                                 void *d_out, int64_t out_cap_spectra, int64_t *out_ticket) {
+    clear_error();
+    if (!server || !out_ticket) return fail(PFB_ERR_INVALID, "NULL argument");
+    *out_ticket = 0;
+    Server &s = *reinterpret_cast<Server *>(server);
+    const auto t0 = Clock::now();
+    std::unique_lock<std::mutex> lk(s.mu);
+    auto it = s.streams.find(stream_id);
+    if (it == s.streams.end() || it->second->closing) return fail(PFB_ERR_INVALID, "unknown stream");
+    PStream &ps = *it->second;
+    const Plan &plan = *ps.plan;
+    if (n_samples <= 0 || n_samples % plan.P != 0) return fail(PFB_ERR_INVALID, "chunk length must be a positive multiple of P");
+    if (!d_chunk || (reinterpret_cast<uintptr_t>(d_chunk) & 15u)) return fail(PFB_ERR_INVALID, "chunk must be a 16-byte aligned device pointer");
+    const int64_t S = next_spectra_locked(ps, n_samples);
+    if (S > 0 && (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15u)))
+        return fail(PFB_ERR_INVALID, "output must be a 16-byte aligned device pointer");
+    if (out_cap_spectra < S) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
+    const int64_t bytes = n_samples * plan.esize + S * plan.P * (int64_t)sizeof(float2);
+    if (bytes + ps.state_bytes > s.desc.hbm_budget_bytes) return fail(PFB_ERR_BUSY, "request larger than the budget");
+    const bool fits = s.queue.empty() && (int64_t)s.inflight.size() < s.desc.max_slots &&
+                      s.reserved + bytes <= s.desc.hbm_budget_bytes;
+    if (!fits && !s.desc.queue_when_busy) {
+        s.n_rejected++;
+        return fail(PFB_ERR_BUSY, "no slot or budget free");
+    }
+    auto r = std::make_unique<Request>();
+    r->ticket = s.next_ticket++;
+    r->stream_id = stream_id;
+    r->d_chunk = d_chunk;
+    r->d_out = d_out;
+    r->n_samples = n_samples;
+    r->S = S;
+    r->bytes = bytes;
+    r->t_submit = t0;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != s.device) cudaSetDevice(s.device);
+    cudaError_t e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (prev != s.device) cudaSetDevice(prev);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    ps.frames_submitted += n_samples / plan.P;
+    ps.outstanding++;
+    s.n_submitted++;
+    Request *rp = r.get();
+    *out_ticket = r->ticket;
+    s.tickets[r->ticket] = std::move(r);
+    s.queue.push_back(rp);
+    admit(s);  // launch right away when a slot and budget are free
+    if (prev != s.device) cudaSetDevice(prev);
+    lk.unlock();
+    s.cv_work.notify_all();
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_poll(pfb_server_t server, int64_t ticket) {
+    if (!server) return PFB_ERR_INVALID;
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.tickets.find(ticket);
+    if (it == s.tickets.end()) return PFB_ERR_INVALID;
+    return it->second->status;
+}
+
+extern "C" pfb_status pfb_wait(pfb_server_t server, int64_t ticket, int32_t timeout_ms) {
+    clear_error();
+    if (!server) return fail(PFB_ERR_INVALID, "server is NULL");
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::unique_lock<std::mutex> lk(s.mu);
+    auto it = s.tickets.find(ticket);
+    if (it == s.tickets.end()) return fail(PFB_ERR_INVALID, "unknown ticket");
+    Request *r = it->second.get();
+    const bool ok = s.cv_done.wait_for(lk, std::chrono::milliseconds(std::max(timeout_ms, 0)),
+                                       [&] { return r->status != PFB_PENDING; });
+    if (!ok) return fail(PFB_ERR_TIMEOUT, "wait timed out");
+    return r->status;
+}
+
+extern "C" pfb_status pfb_server_get_stats(pfb_server_t server, pfb_server_stats *out) {
+    clear_error();
+    if (!server || !out) return fail(PFB_ERR_INVALID, "NULL argument");
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::lock_guard<std::mutex> lk(s.mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s.n_submitted;
+    out->completed = s.n_completed;
+    out->failed = s.n_failed;
+    out->rejected = s.n_rejected;
+    out->queued_now = (int64_t)s.queue.size();
+    out->in_flight_now = (int64_t)s.inflight.size();
+    out->reserved_bytes_now = s.reserved;
+    out->peak_reserved_bytes = s.peak_reserved;
+    out->samples_completed = s.samples_completed;
+    if (!s.latencies_us.empty()) {
+        std::vector<double> v = s.latencies_us;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            size_t idx = (size_t)std::min<double>(v.size() - 1, std::floor(q * (v.size() - 1) + 0.5));
+            return v[idx];
+        };
+        out->p50_latency_us = pct(0.50);
+        out->p99_latency_us = pct(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        out->mean_latency_us = sum / v.size();
+    }
+    return PFB_OK;
+}

@@ -1,0 +1,199 @@
+"""Parity of the FFT path (fused FIR + radix FFT, FP32) with the FP64 oracle,
+through the C ABI.  Sizes span several work units and a ragged tail."""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2408_16551_gb300 as pkg
+from paper_2408_16551_gb300 import synth
+
+from gpu_common import TOL_F32, assert_close, reference, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_16551_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _run(P, T, in_dtype, n, window=synth.WIN_HANN, seed=0, scale=1.0):
+    import torch
+    spec = synth.small_stream(P, T, n, in_dtype=in_dtype, seed=seed, window=window)
+    x = spec.generate()
+    plan = pkg.Plan(P, T, in_dtype, window, pkg.PFB_DFT_FFT_F32, in_scale=scale)
+    X = plan.execute(to_device(x))
+    torch.cuda.synchronize()
+    return plan, x, X.cpu().numpy()
+
+
+FAST = [(P, T, dt) for P in (64, 128, 256, 512, 1024)
+        for (T, dt) in ((16, synth.IN_C64), (8, synth.IN_R32), (4, synth.IN_CI8), (3, synth.IN_C64),
+                        (1, synth.IN_C64), (12, synth.IN_CI8))]
+GENERIC = [(4, 2, synth.IN_C64), (8, 3, synth.IN_R32), (16, 4, synth.IN_R32), (32, 16, synth.IN_CI8),
+           (64, 17, synth.IN_C64), (1024, 64, synth.IN_C64), (2048, 16, synth.IN_C64), (4096, 16, synth.IN_CI8),
+           (4096, 8, synth.IN_C64)]
+
+
+@pytest.mark.parametrize("P,T,dt", FAST + GENERIC)
+def test_fft_path_parity(P, T, dt):
+    n = P * (T - 1 + 8 * 5 + 3) + 7          # 5 full units + 3 spectra + a partial frame
+    plan, x, got = _run(P, T, dt, n, seed=P + T)
+    ref = reference(x, dt, P, T, synth.WIN_HANN)
+    assert got.shape == (plan.out_spectra(n), P)
+    assert_close(got, ref, what=f"{plan.kernel_name} P={P} T={T} dt={dt}")
+
+
+def test_fast_family_is_selected():
+    for P, T in ((64, 16), (1024, 16), (256, 8)):
+        assert pkg.Plan(P, T).kernel_name == "pfb_fir_fft_f32"
+    assert pkg.Plan(4096, 16).kernel_name == "pfb_fir_fft_f32_generic"
+
+
+@pytest.mark.parametrize("P,T", [(64, 4), (1024, 16), (4096, 16), (16, 4)])
+def test_zero_spectra_is_a_noop(P, T):
+    import torch
+    plan = pkg.Plan(P, T)
+    for n in (0, P - 1, P * T - 1):
+        assert plan.out_spectra(n) == 0
+        x = torch.zeros(max(n, 1), dtype=torch.complex64, device="cuda")[:n]
+        out = torch.full((2, P), 7.0, dtype=torch.complex64, device="cuda")
+        plan.execute(x, out=out)
+        torch.cuda.synchronize()
+        assert torch.all(out == 7.0)
+
+
+@pytest.mark.parametrize("P,T", [(64, 4), (1024, 16), (4096, 16)])
+def test_exactly_one_spectrum_and_output_capacity(P, T):
+    import torch
+    n = P * T
+    plan, x, got = _run(P, T, synth.IN_C64, n, seed=5)
+    assert got.shape == (1, P)
+    assert_close(got, reference(x, synth.IN_C64, P, T, synth.WIN_HANN))
+    small = torch.empty((0, P), dtype=torch.complex64, device="cuda")
+    with pytest.raises(pkg.PFBError) as ei:
+        plan.execute(to_device(x), out=small)
+    assert ei.value.status == pkg.PFB_ERR_INVALID
+
+
+def test_config1_real_input():
+    spec = synth.config_c1()
+    x = spec.generate()
+    plan = pkg.Plan(spec.P, spec.T, pkg.PFB_IN_R32, spec.window)
+    got = plan.execute(to_device(x)).cpu().numpy()
+    ref = reference(x, synth.IN_R32, spec.P, spec.T, spec.window)
+    assert got.shape == (1021, 16)
+    assert_close(got, ref, what="c1")
+    assert_close(got[:253], ref[:253], what="c1 first 253 rows")
+
+
+def test_config2_full_size_sampled():
+    """2^24 complex samples, P=1024, T=16: compare sampled spectra one by one."""
+    import torch
+    spec = synth.config_c2()
+    x = spec.generate()
+    plan = pkg.Plan(spec.P, spec.T, pkg.PFB_IN_C64, spec.window)
+    X = plan.execute(to_device(x))
+    torch.cuda.synchronize()
+    S = plan.out_spectra(x.size)
+    assert X.shape == (S, spec.P) == (16369, 1024)
+    rng = np.random.default_rng(99)
+    rows = sorted(set([0, 1, 7, 8, S // 2, S - 9, S - 2, S - 1] + list(rng.integers(0, S, 24))))
+    h = oracle.prototype(spec.P, spec.T, spec.window)
+    xs = oracle.dequant(x, oracle.IN_C64)
+    got = X[rows].cpu().numpy()
+    ref = np.concatenate([oracle.pfb(xs, spec.P, spec.T, h, s0=int(r), ns=1) for r in rows])
+    assert_close(got, ref, what="c2 sampled")
+    # every spectrum is finite and the tones sit in their channels
+    Xa = X.abs().mean(dim=0).cpu().numpy()
+    tone_bins = [c for (c, _, _) in spec.tones]
+    assert set(np.argsort(Xa)[-len(tone_bins):]) == set(tone_bins)
+    assert torch.isfinite(X.view(torch.float32)).all()
+
+
+def test_deterministic_bitwise():
+    import torch
+    P, T = 1024, 16
+    spec = synth.small_stream(P, T, P * 200, seed=1)
+    xd = to_device(spec.generate())
+    plan = pkg.Plan(P, T)
+    a = plan.execute(xd).clone()
+    b = plan.execute(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_taps_generated_on_gpu_match_oracle():
+    for (P, T, w) in ((16, 4, pkg.PFB_WIN_HANN), (1024, 16, pkg.PFB_WIN_HAMMING), (4096, 16, pkg.PFB_WIN_BLACKMAN),
+                      (256, 8, pkg.PFB_WIN_HANN)):
+        h_gpu = pkg.Plan(P, T, window=w).taps()
+        h_ref = oracle.prototype(P, T, w)
+        assert np.max(np.abs(h_gpu - h_ref)) <= 1e-14 * np.max(np.abs(h_ref)) * 10
+
+
+def test_user_taps():
+    P, T = 256, 8
+    rng = np.random.default_rng(4)
+    taps = rng.standard_normal(P * T)
+    spec = synth.small_stream(P, T, P * 60, seed=8)
+    x = spec.generate()
+    plan = pkg.Plan(P, T, window=pkg.PFB_WIN_USER, user_taps=taps)
+    assert np.array_equal(plan.taps(), taps)
+    got = plan.execute(to_device(x)).cpu().numpy()
+    ref = reference(x, synth.IN_C64, P, T, synth.WIN_USER, user_taps=taps)
+    assert_close(got, ref, what="user taps")
+
+
+def test_int8_scale():
+    P, T = 512, 16
+    spec = synth.small_stream(P, T, P * 70, in_dtype=synth.IN_CI8, seed=2)
+    x = spec.generate()
+    plan = pkg.Plan(P, T, pkg.PFB_IN_CI8, in_scale=0.125)
+    got = plan.execute(to_device(x)).cpu().numpy()
+    ref = reference(x, synth.IN_CI8, P, T, synth.WIN_HANN, scale=0.125)
+    assert_close(got, ref, what="int8 scaled")
+
+
+def test_batch_equals_single_bitwise():
+    import torch
+    shapes = [(256, 8, synth.IN_C64, 256 * 300 + 5), (1024, 16, synth.IN_C64, 1024 * 100),
+              (1024, 16, synth.IN_C64, 1024 * 15), (4096, 16, synth.IN_C64, 4096 * 40),
+              (512, 16, synth.IN_CI8, 512 * 77), (16, 4, synth.IN_R32, 16 * 999), (256, 8, synth.IN_C64, 256 * 33)]
+    entries, singles = [], []
+    for i, (P, T, dt, n) in enumerate(shapes):
+        x = to_device(synth.small_stream(P, T, n, in_dtype=dt, seed=30 + i).generate())
+        plan = pkg.Plan(P, T, dt, window=i % 3)
+        S = plan.out_spectra(n)
+        out = torch.zeros((max(S, 1), P), dtype=torch.complex64, device="cuda")
+        entries.append((plan, x, out))
+        singles.append(plan.execute(x).clone() if S > 0 else None)
+    pkg.pfb_execute_batch(entries)
+    torch.cuda.synchronize()
+    for (plan, x, out), ref in zip(entries, singles):
+        if ref is not None:
+            assert torch.equal(out[:ref.shape[0]], ref)
+    for (_, _, out) in entries:
+        out.zero_()
+    b = pkg.Batch(entries)
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    for (plan, x, out), ref in zip(entries, singles):
+        if ref is not None:
+            assert torch.equal(out[:ref.shape[0]], ref)
+
+
+def test_execute_host_matches_device():
+    import torch
+    P, T = 1024, 16
+    x = synth.small_stream(P, T, P * 90 + 3, seed=6).generate()
+    plan = pkg.Plan(P, T)
+    dev = plan.execute(to_device(x)).cpu().numpy()
+    host = plan.execute_host(x)
+    assert np.array_equal(dev, host)

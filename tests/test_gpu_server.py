@@ -1,0 +1,198 @@
+"""Serving: resident filter state, continuous batching, admission, faults
+injected on the host (no GPU fault is provoked)."""
+
+import os
+import time
+
+import numpy as np
+import pytest
+
+import paper_2408_16551_gb300 as pkg
+from paper_2408_16551_gb300 import synth
+
+from gpu_common import assert_close, reference, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_16551_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _chunked(server, plan, x, chunk):
+    """Submit x in chunks of `chunk` samples; return the concatenated outputs."""
+    import torch
+    sid = server.open_stream(plan)
+    per = 2 if plan.in_dtype == pkg.PFB_IN_CI8 else 1
+    n = x.numel() // per
+    outs, tickets = [], []
+    for c0 in range(0, n, chunk):
+        part = x[c0 * per:(c0 + chunk) * per]
+        S = server.next_spectra(sid, chunk)
+        out = torch.empty((max(S, 1), plan.P), dtype=torch.complex64, device="cuda")
+        tickets.append(server.submit(sid, part, chunk, out))
+        outs.append(out[:S])
+    for t in tickets:
+        assert server.wait(t, 20000) == pkg.PFB_OK
+    server.close_stream(sid)
+    return torch.cat(outs)
+
+
+@pytest.mark.parametrize("P,T,dt,chunk,nchunks", [(1024, 16, synth.IN_C64, 1 << 14, 9),
+                                                  (4096, 16, synth.IN_CI8, 1 << 16, 4),
+                                                  (256, 8, synth.IN_C64, 256 * 3, 11),
+                                                  (64, 16, synth.IN_R32, 64 * 5, 12)])
+def test_chunked_stream_equals_whole_stream(P, T, dt, chunk, nchunks):
+    import torch
+    n = chunk * nchunks
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=P).generate()
+    xd = to_device(x)
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_BLACKMAN)
+    whole = plan.execute(xd)
+    srv = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=4)
+    got = _chunked(srv, plan, xd, chunk)
+    torch.cuda.synchronize()
+    assert got.shape == whole.shape
+    assert torch.equal(got, whole)          # same kernel, same summation order
+    assert_close(got.cpu().numpy(), reference(x, dt, P, T, synth.WIN_BLACKMAN), what="chunked vs oracle")
+    assert srv.close() == pkg.PFB_OK
+
+
+def test_alone_equals_in_mix():
+    import torch
+    P, T, chunk = 1024, 16, 1 << 14
+    plan = pkg.Plan(P, T)
+    xs = [to_device(synth.small_stream(P, T, chunk * 6, seed=40 + i).generate()) for i in range(6)]
+    srv = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=8)
+    alone = _chunked(srv, plan, xs[0], chunk)
+    # now stream 0 again, interleaved with five other streams in flight
+    sids = [srv.open_stream(plan) for _ in xs]
+    outs = [[] for _ in xs]
+    tickets = []
+    for c in range(6):
+        for i, sid in enumerate(sids):
+            S = srv.next_spectra(sid, chunk)
+            out = torch.empty((S, P), dtype=torch.complex64, device="cuda")
+            tickets.append(srv.submit(sid, xs[i][c * chunk:(c + 1) * chunk], chunk, out))
+            outs[i].append(out)
+    for t in tickets:
+        assert srv.wait(t, 20000) == pkg.PFB_OK
+    mixed = torch.cat(outs[0])
+    assert torch.equal(mixed, alone)
+    st = srv.stats()
+    assert st["completed"] == 6 + 36 and st["failed"] == 0
+    assert st["p99_latency_us"] >= st["p50_latency_us"] > 0
+    assert srv.close() == pkg.PFB_OK
+
+
+def test_admission_by_budget_queues_and_completes():
+    import torch
+    P, T, chunk = 1024, 16, 1 << 14
+    plan = pkg.Plan(P, T)
+    req_bytes = chunk * 8 + (chunk // P) * P * 8
+    state_bytes = 2 * (T - 1) * P * 8
+    nstreams = 4
+    budget = nstreams * state_bytes + 2 * req_bytes       # at most two requests on the device
+    srv = pkg.Server(hbm_budget_bytes=budget, max_slots=8, queue_when_busy=True)
+    sids = [srv.open_stream(plan) for _ in range(nstreams)]
+    x = to_device(synth.small_stream(P, T, chunk, seed=1).generate())
+    tickets = []
+    for rep in range(5):
+        for sid in sids:
+            S = srv.next_spectra(sid, chunk)
+            out = torch.empty((max(S, 1), P), dtype=torch.complex64, device="cuda")
+            tickets.append((srv.submit(sid, x, chunk, out), out))
+    for t, _ in tickets:
+        assert srv.wait(t, 20000) == pkg.PFB_OK
+    st = srv.stats()
+    assert st["peak_reserved_bytes"] <= budget
+    assert st["completed"] == 20
+    assert srv.close() == pkg.PFB_OK
+
+
+def test_busy_when_not_queuing():
+    import torch
+    P, T, chunk = 4096, 16, 1 << 16
+    plan = pkg.Plan(P, T)
+    srv = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=1, queue_when_busy=False)
+    sid = srv.open_stream(plan)
+    big = to_device(synth.small_stream(P, T, chunk * 64, seed=2).generate())
+    got_busy = False
+    tickets = []
+    for c in range(64):
+        S = srv.next_spectra(sid, chunk)
+        out = torch.empty((max(S, 1), P), dtype=torch.complex64, device="cuda")
+        try:
+            tickets.append(srv.submit(sid, big[c * chunk:(c + 1) * chunk], chunk, out))
+        except pkg.PFBError as e:
+            assert e.status == pkg.PFB_ERR_BUSY
+            got_busy = True
+            break
+    for t in tickets:
+        assert srv.wait(t, 20000) == pkg.PFB_OK
+    assert got_busy
+    assert srv.stats()["rejected"] >= 1
+    srv.close()
+
+
+def test_invalid_submissions():
+    import torch
+    plan = pkg.Plan(1024, 16)
+    srv = pkg.Server(hbm_budget_bytes=1 << 30, max_slots=2)
+    sid = srv.open_stream(plan)
+    x = torch.zeros(1024 * 20 + 5, dtype=torch.complex64, device="cuda")
+    out = torch.empty((20, 1024), dtype=torch.complex64, device="cuda")
+    with pytest.raises(pkg.PFBError) as ei:
+        srv.submit(sid, x, 1024 * 20 + 5, out)            # not a multiple of P
+    assert ei.value.status == pkg.PFB_ERR_INVALID
+    with pytest.raises(pkg.PFBError):
+        srv.submit(sid + 100, x, 1024 * 20, out)            # unknown stream
+    with pytest.raises(pkg.PFBError):
+        srv.submit(sid, x, 1024 * 20, out[:1])              # output too small
+    srv.close()
+
+
+def test_injected_launch_failure_fails_only_that_request(monkeypatch):
+    import torch
+    monkeypatch.setenv("PFB_FAULT", "launch_fail:3")
+    P, T, chunk = 1024, 16, 1 << 13
+    plan = pkg.Plan(P, T)
+    srv = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=4)
+    monkeypatch.delenv("PFB_FAULT")
+    sids = [srv.open_stream(plan) for _ in range(5)]
+    x = to_device(synth.small_stream(P, T, chunk, seed=3).generate())
+    tickets = []
+    for sid in sids:
+        out = torch.empty((max(srv.next_spectra(sid, chunk), 1), P), dtype=torch.complex64, device="cuda")
+        tickets.append((srv.submit(sid, x, chunk, out), out))
+    res = [srv.wait(t, 20000) for t, _ in tickets]
+    assert res.count(pkg.PFB_ERR_CUDA) == 1 and res.count(pkg.PFB_OK) == 4
+    assert res[2] == pkg.PFB_ERR_CUDA
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 4
+    assert srv.close() == pkg.PFB_OK
+
+
+def test_lost_completion_times_out(monkeypatch):
+    import torch
+    monkeypatch.setenv("PFB_FAULT", "lose_completion:2")
+    P, T, chunk = 256, 8, 256 * 16
+    plan = pkg.Plan(P, T)
+    srv = pkg.Server(hbm_budget_bytes=1 << 30, max_slots=4, timeout_ms=200)
+    monkeypatch.delenv("PFB_FAULT")
+    sids = [srv.open_stream(plan) for _ in range(3)]
+    x = to_device(synth.small_stream(P, T, chunk, seed=4).generate())
+    tickets = []
+    for sid in sids:
+        out = torch.empty((max(srv.next_spectra(sid, chunk), 1), P), dtype=torch.complex64, device="cuda")
+        tickets.append((srv.submit(sid, x, chunk, out), out))
+    res = [srv.wait(t, 5000) for t, _ in tickets]
+    assert res == [pkg.PFB_OK, pkg.PFB_ERR_TIMEOUT, pkg.PFB_OK]
+    # the lost request still holds its slot, so destroy reports a timeout
+    assert srv.close() == pkg.PFB_ERR_TIMEOUT
