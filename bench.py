@@ -330,6 +330,7 @@ def main():
     n = int(x.size)
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_FFT_F32)
     S = plan.out_spectra(n)
+    tune_ms = plan.autotune(n) if not args.minimal else None  # tile shape from the autotuner
     nsets = max(1, args.nsets)  # rotating input/output sets: 4 x 256 MiB > 129 MB L2
     xd0 = torch.from_numpy(x).to(device)
     xs = [xd0] + [xd0.clone() for _ in range(nsets - 1)]
@@ -389,6 +390,7 @@ def main():
         "config": {"workload": "c2: one stream of 2^24 complex64 samples (CN(0,1) + 8 channel-centre tones), "
                                "P=1024, T=16, Hamming-windowed sinc prototype; FIR + FFT path (FP32)",
                    "P": P, "T": T, "n_samples": n, "spectra": S, "path": "fft_f32",
+                   "variant": plan.variant,
                    "l2": f"{nsets} rotating input/output buffer sets ({nsets * (n * 8 + S * P * 8) >> 20} MiB) > 129 MB L2",
                    "replicas": "each rank channelises its own copy of the workload (weak scaling, no collective)"},
         "roofline": roofline,

@@ -159,6 +159,25 @@ PFB_API pfb_status pfb_batch_launch(pfb_batch_t batch, void *cuda_stream);
 PFB_API pfb_status pfb_batch_destroy(pfb_batch_t batch);
 
 /* ---------------------------------------------------------------------- */
+/* Autotuning: kernel variants (tile shapes) of a plan's kernel family     */
+/* ---------------------------------------------------------------------- */
+
+/* Number of kernel variants the plan's family offers (>= 1), and the one in
+ * use.  A new plan starts from the variant cached for its shape (see
+ * pfb_plan_autotune) or from a built-in default. */
+PFB_API int32_t pfb_plan_num_variants(pfb_plan_t plan);
+PFB_API int32_t pfb_plan_variant(pfb_plan_t plan);
+/* Select a variant explicitly (0 <= variant < pfb_plan_num_variants). */
+PFB_API pfb_status pfb_plan_set_variant(pfb_plan_t plan, int32_t variant);
+/* Time every variant on an input of n_samples (device scratch buffers the
+ * call allocates, fills and frees; it synchronises cuda_stream), keep the
+ * fastest in the plan and cache it per (GPU, P, T, dtype, family) -- in the
+ * process, and in the JSON file named by the environment variable
+ * PFB_AUTOTUNE_CACHE if set.  out_best_ms (may be NULL) receives the winner's
+ * time per pfb_execute. */
+PFB_API pfb_status pfb_plan_autotune(pfb_plan_t plan, int64_t n_samples, void *cuda_stream, double *out_best_ms);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of channelisation requests                */
 /* ---------------------------------------------------------------------- */
 

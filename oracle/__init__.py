@@ -174,6 +174,48 @@ def pfb_input(x: np.ndarray, in_dtype: int, P: int, T: int, h: np.ndarray, scale
     return pfb(dequant(x, in_dtype, scale), P, T, h, s0=s0, ns=ns, threads=threads)
 
 
+# --------------------------------------------------------------------------
+# split-bf16 arithmetic model of the tensor-core DFT path (test-side model of
+# what the kernel computes, used to separate split error from indexing bugs)
+# --------------------------------------------------------------------------
+
+def bf16_round(v) -> np.ndarray:
+    """Round to the nearest bfloat16 value (8 significant bits, ties to even), in float64."""
+    v = np.asarray(v, dtype=np.float64)
+    m, e = np.frexp(v)                      # v = m 2^e, |m| in [0.5, 1)
+    return np.ldexp(np.round(m * 256.0), e - 8)
+
+
+def dft_block_matrix(P: int) -> np.ndarray:
+    """Real block form of the Fourier matrix of Sec. 4.1 on interleaved (re, im)
+    rows/columns: B[2p+c, 2k+d] with th = 2 pi (pk mod P)/P:
+    B[2p,2k] = B[2p+1,2k+1] = cos th, B[2p+1,2k] = sin th, B[2p,2k+1] = -sin th."""
+    p = np.arange(P)[:, None]
+    k = np.arange(P)[None, :]
+    th = 2.0 * np.pi * ((p * k) % P) / P
+    B = np.zeros((2 * P, 2 * P))
+    B[0::2, 0::2] = np.cos(th)
+    B[1::2, 1::2] = np.cos(th)
+    B[1::2, 0::2] = np.sin(th)
+    B[0::2, 1::2] = -np.sin(th)
+    return B
+
+
+def split_bf16x3_model(y32: np.ndarray, P: int) -> np.ndarray:
+    """X = A_hi (B_hi + B_lo) + A_lo B_hi in FP64, with A = interleaved fp32
+    branch sums split into bf16 hi/lo and B split from its FP64 value."""
+    A = np.empty((y32.shape[0], 2 * P))
+    A[:, 0::2] = np.asarray(y32.real, dtype=np.float32)
+    A[:, 1::2] = np.asarray(y32.imag, dtype=np.float32)
+    Ah = bf16_round(A)
+    Al = bf16_round(A - Ah)
+    B = dft_block_matrix(P)
+    Bh = bf16_round(B)
+    Bl = bf16_round(B - Bh)
+    Xr = Ah @ (Bh + Bl) + Al @ Bh
+    return Xr[:, 0::2] + 1j * Xr[:, 1::2]
+
+
 def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
     """||a - ref||_2 / ||ref||_2 in FP64 (the parity metric)."""
     a = np.asarray(a, dtype=np.complex128); ref = np.asarray(ref, dtype=np.complex128)

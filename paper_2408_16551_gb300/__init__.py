@@ -36,6 +36,7 @@ EXPORTED = [
     "pfb_server_create", "pfb_server_destroy", "pfb_stream_open", "pfb_stream_close",
     "pfb_stream_next_spectra", "pfb_submit", "pfb_poll", "pfb_wait", "pfb_server_get_stats",
     "pfb_status_string", "pfb_last_error", "pfb_launch_count", "pfb_plan_kernel_name",
+    "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
 ]
 
 
@@ -114,6 +115,10 @@ def lib() -> ctypes.CDLL:
             "pfb_last_error": (ctypes.c_char_p, []),
             "pfb_launch_count": (i64, []),
             "pfb_plan_kernel_name": (ctypes.c_char_p, [vp]),
+            "pfb_plan_num_variants": (i32, [vp]),
+            "pfb_plan_variant": (i32, [vp]),
+            "pfb_plan_set_variant": (st, [vp, i32]),
+            "pfb_plan_autotune": (st, [vp, i64, vp, ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -191,6 +196,25 @@ class Plan:
     @property
     def kernel_name(self) -> str:
         return lib().pfb_plan_kernel_name(self.handle).decode()
+
+    @property
+    def variant(self) -> int:
+        return int(lib().pfb_plan_variant(self.handle))
+
+    @variant.setter
+    def variant(self, v: int):
+        _check(lib().pfb_plan_set_variant(self.handle, v), "pfb_plan_set_variant")
+
+    @property
+    def num_variants(self) -> int:
+        return int(lib().pfb_plan_num_variants(self.handle))
+
+    def autotune(self, n_samples: int, stream=None) -> float:
+        """pfb_plan_autotune: time each variant, keep the fastest; returns its ms per call."""
+        ms = ctypes.c_double()
+        _check(lib().pfb_plan_autotune(self.handle, n_samples, _stream_handle(stream), ctypes.byref(ms)),
+               "pfb_plan_autotune")
+        return ms.value
 
     def out_spectra(self, n_samples: int) -> int:
         return int(lib().pfb_out_spectra(self.handle, n_samples))

@@ -25,13 +25,13 @@ pfb_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 int64_t generic_units(int P, int64_t S);
-int64_t fast_units(int64_t S);
+int64_t fast_units(const Plan &plan, int64_t S);
 int64_t gemm_f32_units(const Plan &plan, int64_t S);
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S);
 
 int64_t family_units(const Plan &plan, int64_t S) {
     switch (plan.family) {
-    case FAM_FFT_FAST: return fast_units(S);
+    case FAM_FFT_FAST: return fast_units(plan, S);
     case FAM_FFT_GENERIC: return generic_units(plan.P, S);
     case FAM_GEMM_F32: return gemm_f32_units(plan, S);
     case FAM_GEMM_BF16X3: return gemm_bf16x3_units(plan, S);
@@ -39,9 +39,7 @@ int64_t family_units(const Plan &plan, int64_t S) {
     }
 }
 
-static const float *family_taps(const Plan &plan) {
-    return plan.family == FAM_FFT_FAST ? plan.d_taps_pad : plan.d_taps;
-}
+const float *family_taps(const Plan &plan) { return plan.d_taps_pad ? plan.d_taps_pad : plan.d_taps; }
 
 // Launch the plan's family kernel over n stream descriptors (all of this
 // family/P/T/dtype), in groups of kMaxStreamsPerLaunch.
@@ -214,7 +212,7 @@ struct Group {
 
 static pfb_status build_groups(const pfb_batch_item *items, int32_t n, std::vector<Group> &groups, int &device) {
     if (n < 0 || (n > 0 && !items)) return fail(PFB_ERR_INVALID, "bad item list");
-    std::map<std::tuple<int, int, int, int>, size_t> index;
+    std::map<std::tuple<int, int, int, int, int>, size_t> index;
     device = -1;
     for (int i = 0; i < n; ++i) {
         const pfb_batch_item &it = items[i];
@@ -228,7 +226,7 @@ static pfb_status build_groups(const pfb_batch_item *items, int32_t n, std::vect
         if (d.S == 0) continue;
         // streams share a launch when the kernel variant is the same; taps are
         // per stream (descriptor), twiddles/DFT tables depend only on P
-        auto key = std::make_tuple(p.family, p.P, p.TT, p.in_dtype);
+        auto key = std::make_tuple(p.family, p.P, p.TT, p.in_dtype, p.variant);
         auto f = index.find(key);
         if (f == index.end()) {
             index[key] = groups.size();

@@ -1,26 +1,30 @@
 // Fused polyphase FIR + radix-16 Stockham FFT, FP32 (fast FFT family).
 //
-// Computes, for each work unit of kSB consecutive spectra of one stream,
+// Computes, for each work unit of SB consecutive spectra of one stream,
 //   y[s,p] = sum_{m<T} h[m*P+p] * x[(s+m)*P+p]        (Sec. 5.2, FIR per branch,
 //                                                       Sec. 4.3 correlation form)
 //   X[s,k] = sum_p y[s,p] exp(-2 pi i p k / P)          (Sec. 4.1, the DFT)
 // with the branch sums y kept in shared memory (they never go back to HBM).
 //
-// Mapping (P in [64, 1024], T <= 16 padded with zero taps to TT in {4,8,16}):
-//   - one CTA of P/2 threads; thread t owns the branch pair (2t, 2t+1) and
-//     keeps its 2*TT fp32 taps in registers for as long as it stays on a stream;
-//   - the FIR of a unit reads kSB+TT-1 frames, one 16-byte (C64) load per
-//     frame per thread: coalesced, read-only path, each load reused by up to
-//     kSB spectra in registers (the TT-1 frame halo is re-read from L1/L2);
-//   - the kSB rows of branch sums go to shared memory (rows padded by one
-//     slot every 16 entries: all passes are bank-conflict free), then an
-//     in-place Stockham autosort FFT runs pass by pass: radix 16 first, one
-//     final radix in {2,4,8,16}; each thread carries 16 complex values per
-//     pass, twiddles come from a table built in FP64 at plan time;
+// Mapping (P in [64, 1024], T <= 16 zero-extended to TT in {4,8,16}):
+//   - one CTA of NT = P/NB threads, NB in {2, 4} consecutive branches per
+//     thread, SB = 16/NB spectra per unit; the thread's NB*TT fp32 taps stay
+//     in registers while it works on a stream;
+//   - the FIR of a unit reads SB+TT-1 frames, one 16/32-byte vector load per
+//     frame per thread (coalesced, read-only path), each load reused by up to
+//     SB spectra in registers; interior units take an unguarded path whose
+//     addresses are one base pointer plus compile-time offsets;
+//   - the SB rows of branch sums go to shared memory (one pad slot every 16
+//     entries: every pass is bank-conflict free), then an in-place Stockham
+//     autosort FFT runs pass by pass: radix 16 first, one final radix in
+//     {2,4,8,16}; each thread carries 16 complex values per pass; shared and
+//     twiddle addresses are a per-thread base plus compile-time offsets;
+//     twiddles come from a table built in FP64 at plan time;
 //   - the last pass stores natural-order bins straight from registers with
-//     streaming 8-byte stores, coalesced across the warp.
-// A CTA walks a contiguous range of work units (persistent grid sized to the
-// resident capacity), so consecutive units reuse their frames from L1.
+//     streaming 8-byte stores, coalesced across the warp;
+//   - a CTA walks a contiguous range of units (persistent grid sized to the
+//     resident capacity); one thread issues an L2 bulk prefetch of the
+//     frames the unit after next will need.
 #pragma once
 
 #include "devutil.cuh"
@@ -29,63 +33,143 @@
 
 namespace pfb {
 
-constexpr int kSB = 8;  // spectra per work unit (FFT batch)
-
-template <int P>
+template <int P, int NB>
 struct FastCfg {
-    static constexpr int NT = P / 2;
+    static constexpr int NT = P / NB;
+    static constexpr int SB = 16 / NB;
     static constexpr int YROW = P + P / 16;
     static constexpr int NTW = fft_tw_entries(P);
-    static constexpr size_t SMEM = (size_t)(kSB * YROW + (NTW > 0 ? NTW : 1)) * sizeof(float2);
+    static constexpr size_t SMEM = (size_t)(SB * YROW + (NTW > 0 ? NTW : 1)) * sizeof(float2);
+    static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;
 };
 
 __device__ __forceinline__ int ypad(int i) { return i + (i >> 4); }
 
-template <int P, int PASS>
+// packed fp32x2 arithmetic (Blackwell): two lanes of fp32 per instruction
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tmov.b64 rc, {%6,%7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// loads of NB consecutive branches of one frame
+// ---------------------------------------------------------------------------
+template <int IN, int NB>
+__device__ __forceinline__ void load_nb(const void *base, int64_t idx, float s, float2 (&v)[NB]) {
+    if constexpr (IN == PFB_IN_C64) {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float2 *>(base) + idx);
+#pragma unroll
+        for (int k = 0; k < NB / 2; ++k) {
+            float4 w = __ldg(p + k);
+            v[2 * k] = make_float2(w.x, w.y);
+            v[2 * k + 1] = make_float2(w.z, w.w);
+        }
+    } else if constexpr (IN == PFB_IN_R32) {
+        if constexpr (NB == 4) {
+            float4 w = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(base) + idx));
+            v[0] = make_float2(w.x, 0.f); v[1] = make_float2(w.y, 0.f);
+            v[2] = make_float2(w.z, 0.f); v[3] = make_float2(w.w, 0.f);
+        } else {
+            float2 w = __ldg(reinterpret_cast<const float2 *>(static_cast<const float *>(base) + idx));
+            v[0] = make_float2(w.x, 0.f); v[1] = make_float2(w.y, 0.f);
+        }
+    } else {
+        const int8_t *b8 = static_cast<const int8_t *>(base) + 2 * idx;
+        if constexpr (NB == 4) {
+            int2 w = __ldg(reinterpret_cast<const int2 *>(b8));
+            char4 a = *reinterpret_cast<char4 *>(&w.x), c = *reinterpret_cast<char4 *>(&w.y);
+            v[0] = make_float2((float)a.x * s, (float)a.y * s); v[1] = make_float2((float)a.z * s, (float)a.w * s);
+            v[2] = make_float2((float)c.x * s, (float)c.y * s); v[3] = make_float2((float)c.z * s, (float)c.w * s);
+        } else {
+            char4 a = __ldg(reinterpret_cast<const char4 *>(b8));
+            v[0] = make_float2((float)a.x * s, (float)a.y * s); v[1] = make_float2((float)a.z * s, (float)a.w * s);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one Stockham pass
+// ---------------------------------------------------------------------------
+template <int P, int NB, int PASS>
 __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float2 *out_row0, int nrows) {
+    using C = FastCfg<P, NB>;
     constexpr int R = fft_radix(P, PASS);
     constexpr int NS = fft_ns(P, PASS);
-    constexpr int NT = FastCfg<P>::NT;
-    constexpr int YROW = FastCfg<P>::YROW;
+    constexpr int NT = C::NT;
+    constexpr int YROW = C::YROW;
     constexpr bool LAST = (PASS == fft_npasses(P) - 1);
-    constexpr int PER = (kSB * P / R) / NT;  // butterflies per thread (16 / R)
+    constexpr int PER = (C::SB * P / R) / NT;  // butterflies per thread
     constexpr int STRIDE = P / R;
     static_assert(PER * R == 16, "each thread carries 16 values per pass");
     const float2 *twp = tw + fft_tw_offset(P, PASS);
+    const int t = threadIdx.x;
+
+    // butterfly q of this thread: b = t + q*NT -> (row, j); both are a
+    // per-thread base plus a compile-time offset
+    auto rowj = [&](int q, int &row, int &j) {
+        if constexpr (NT >= STRIDE) {
+            row = t / STRIDE + q * (NT / STRIDE);
+            j = t % STRIDE;
+        } else {
+            row = q / (STRIDE / NT);
+            j = t + (q % (STRIDE / NT)) * NT;
+        }
+    };
 
     float2 v[PER][R];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * NT;
-        const int row = b / STRIDE, j = b % STRIDE;
+        int row, j;
+        rowj(q, row, j);
+        const float2 *src = Y + row * YROW;
+        if constexpr (STRIDE % 16 == 0) {
+            src += ypad(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = Y[row * YROW + ypad(j + r * STRIDE)];
-        if (NS > 1) {
-            const int jj = j % NS;
+            for (int r = 0; r < R; ++r) v[q][r] = src[r * (STRIDE + STRIDE / 16)];
+        } else {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], twp[jj * (R - 1) + r - 1]);
+            for (int r = 0; r < R; ++r) v[q][r] = src[ypad(j + r * STRIDE)];
+        }
+        if constexpr (NS > 1) {
+            const float2 *w = twp + (j % NS) * (R - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], w[r - 1]);
         }
         dft_reg<R>(v[q]);
     }
-    if (!LAST) {
+    if constexpr (!LAST) {
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-            const int b = threadIdx.x + q * NT;
-            const int row = b / STRIDE, j = b % STRIDE;
-            const int base = (j / NS) * NS * R + (j % NS);
+            int row, j;
+            rowj(q, row, j);
+            float2 *dst = Y + row * YROW;
+            if constexpr (NS == 1) {
+                static_assert(R == 16 || NS > 1, "first pass is radix 16");
+                dst += 17 * j;  // ypad(16 j + r) = 17 j + r
 #pragma unroll
-            for (int r = 0; r < R; ++r) Y[row * YROW + ypad(base + r * NS)] = v[q][r];
+                for (int r = 0; r < R; ++r) dst[r] = v[q][r];
+            } else {
+                static_assert(NS % 16 == 0, "Ns is a multiple of 16 after the first pass");
+                dst += ypad((j / NS) * NS * R + (j % NS));
+#pragma unroll
+                for (int r = 0; r < R; ++r) dst[r * (NS + NS / 16)] = v[q][r];
+            }
         }
         __syncthreads();
     } else {
         // NS * R == P: bin index j + r*NS, natural order
+        const bool full = (nrows == C::SB);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-            const int b = threadIdx.x + q * NT;
-            const int row = b / STRIDE, j = b % STRIDE;
-            if (row < nrows) {
-                float2 *o = out_row0 + (int64_t)row * P + j;
+            int row, j;
+            rowj(q, row, j);
+            if (full || row < nrows) {
+                float2 *o = out_row0 + row * P + j;
 #pragma unroll
                 for (int r = 0; r < R; ++r) store_cs(o + r * NS, v[q][r]);
             }
@@ -93,90 +177,128 @@ __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float
     }
 }
 
-template <int P, int PASS>
+template <int P, int NB, int PASS>
 __device__ __forceinline__ void fft_fast_passes(float2 *Y, const float2 *tw, float2 *out_row0, int nrows) {
-    fft_fast_pass<P, PASS>(Y, tw, out_row0, nrows);
-    if constexpr (PASS + 1 < fft_npasses(P)) fft_fast_passes<P, PASS + 1>(Y, tw, out_row0, nrows);
+    fft_fast_pass<P, NB, PASS>(Y, tw, out_row0, nrows);
+    if constexpr (PASS + 1 < fft_npasses(P)) fft_fast_passes<P, NB, PASS + 1>(Y, tw, out_row0, nrows);
 }
 
-template <int P, int TT, int IN>
-__global__ void __launch_bounds__(P / 2) k_fft_fast(const __grid_constant__ LaunchArgs a) {
-    using L = Loader<IN>;
-    constexpr int NT = FastCfg<P>::NT;
-    constexpr int YROW = FastCfg<P>::YROW;
+// acc[j][b] += h[m][b] * v[b] for the spectra j that frame i feeds
+template <int TT, int SB, int NB, bool REAL, bool PK>
+__device__ __forceinline__ void fir_frame(int i, const float (&h)[TT][NB], const float2 (&v)[NB],
+                                          float2 (&acc)[SB][NB]) {
+#pragma unroll
+    for (int j = 0; j < SB; ++j) {
+        const int m = i - j;
+        if (m >= 0 && m < TT) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if constexpr (REAL) {
+                    acc[j][b].x = fmaf(h[m][b], v[b].x, acc[j][b].x);
+                } else if constexpr (PK) {
+                    acc[j][b] = fma2(make_float2(h[m][b], h[m][b]), v[b], acc[j][b]);
+                } else {
+                    acc[j][b].x = fmaf(h[m][b], v[b].x, acc[j][b].x);
+                    acc[j][b].y = fmaf(h[m][b], v[b].y, acc[j][b].y);
+                }
+            }
+        }
+    }
+}
+
+template <int P, int TT, int IN, int NB, bool PK>
+__global__ void __launch_bounds__(P / NB, FastCfg<P, NB>::MINB) k_fft_fast(const __grid_constant__ LaunchArgs a) {
+    using C = FastCfg<P, NB>;
+    constexpr int NT = C::NT, SB = C::SB, YROW = C::YROW;
+    constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
+    constexpr bool REAL = (IN == PFB_IN_R32);
     extern __shared__ __align__(16) float2 sm[];
     float2 *Y = sm;
-    float2 *tw = sm + kSB * YROW;
+    float2 *tw = sm + SB * YROW;
     const int t = threadIdx.x;
-    for (int i = t; i < FastCfg<P>::NTW; i += NT) tw[i] = a.tw[i];
+    const int q0 = NB * t;  // first branch of this thread
+    for (int i = t; i < C::NTW; i += NT) tw[i] = a.tw[i];
 
     const int64_t u0 = (int64_t)blockIdx.x * a.units_per_cta;
     const int64_t u1 = min(u0 + (int64_t)a.units_per_cta, a.nunits);
     int cur = -1;
-    float h0[TT], h1[TT];
+    float h[TT][NB];
     for (int64_t u = u0; u < u1; ++u) {
         const int si = find_stream(a, u);
         const StreamDesc &d = a.s[si];
         if (si != cur) {
             cur = si;
 #pragma unroll
-            for (int m = 0; m < TT; ++m) {
-                float2 hv = __ldg(reinterpret_cast<const float2 *>(d.taps + m * P + 2 * t));
-                h0[m] = hv.x;
-                h1[m] = hv.y;
+            for (int m = 0; m < TT; ++m)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) h[m][b] = __ldg(d.taps + m * P + q0 + b);
+        }
+        const int64_t s0 = (u - d.unit0) * SB;
+        const int nrows = (int)min((int64_t)SB, d.S - s0);
+
+        // L2 prefetch of the frames first needed by the unit after next
+        if (t == 0) {
+            const int64_t f0 = s0 + 2 * SB + TT - 1;
+            const int64_t f1 = min(f0 + SB, d.n_frames);
+            if (f0 >= d.n_state && f1 > f0) {
+                const char *p = static_cast<const char *>(d.in) + (f0 - d.n_state) * (int64_t)P * ESZ;
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((int)((f1 - f0) * P * ESZ))
+                             : "memory");
             }
         }
-        const int64_t s0 = (u - d.unit0) * kSB;
-        const int nrows = (int)min((int64_t)kSB, d.S - s0);
 
-        // ---- polyphase FIR: kSB spectra x 2 branches, taps in registers ----
-        float2 acc0[kSB], acc1[kSB];
+        // ---- polyphase FIR: SB spectra x NB branches, taps in registers ----
+        float2 acc[SB][NB];
 #pragma unroll
-        for (int j = 0; j < kSB; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < SB; ++j)
 #pragma unroll
-        for (int i = 0; i < kSB + TT - 1; ++i) {
-            const int64_t f = s0 + i;
-            float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-            if (f < d.n_frames) {
-                int64_t smp;
-                const void *src = frame_source(d, f, P, smp);
-                L::load2(src, smp + 2 * t, d.scale, v0, v1);
+            for (int b = 0; b < NB; ++b) acc[j][b] = make_float2(0.f, 0.f);
+        const bool interior = (s0 >= d.n_state) && (s0 + SB + TT - 1 <= d.n_frames);
+        if (interior) {
+            const char *base = static_cast<const char *>(d.in) + ((s0 - d.n_state) * P + q0) * ESZ;
+#pragma unroll
+            for (int i = 0; i < SB + TT - 1; ++i) {
+                float2 v[NB];
+                load_nb<IN, NB>(base + (int64_t)i * P * ESZ, 0, d.scale, v);
+                fir_frame<TT, SB, NB, REAL, PK>(i, h, v, acc);
             }
+        } else {
 #pragma unroll
-            for (int j = 0; j < kSB; ++j) {
-                const int m = i - j;
-                if (m >= 0 && m < TT) {
-                    acc0[j].x = fmaf(h0[m], v0.x, acc0[j].x);
-                    acc1[j].x = fmaf(h1[m], v1.x, acc1[j].x);
-                    if (!L::kReal) {
-                        acc0[j].y = fmaf(h0[m], v0.y, acc0[j].y);
-                        acc1[j].y = fmaf(h1[m], v1.y, acc1[j].y);
-                    }
+            for (int i = 0; i < SB + TT - 1; ++i) {
+                const int64_t f = s0 + i;
+                float2 v[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) v[b] = make_float2(0.f, 0.f);
+                if (f < d.n_frames) {
+                    int64_t smp;
+                    const void *src = frame_source(d, f, P, smp);
+                    load_nb<IN, NB>(src, smp + q0, d.scale, v);
                 }
+                fir_frame<TT, SB, NB, REAL, PK>(i, h, v, acc);
             }
         }
         __syncthreads();  // previous unit's last pass has finished reading Y
-        const int c = ypad(2 * t);
+        const int c = ypad(q0);
 #pragma unroll
-        for (int j = 0; j < kSB; ++j) {
-            Y[j * YROW + c] = acc0[j];
-            Y[j * YROW + c + 1] = acc1[j];
-        }
+        for (int j = 0; j < SB; ++j)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) Y[j * YROW + c + b] = acc[j][b];
         __syncthreads();
-        // ---- P-point FFT of the kSB rows, last pass stores to HBM ----
-        fft_fast_passes<P, 0>(Y, tw, d.out + s0 * P, nrows);
+        // ---- P-point FFT of the SB rows, last pass stores to HBM ----
+        fft_fast_passes<P, NB, 0>(Y, tw, d.out + s0 * P, nrows);
     }
 }
 
 template <int P>
 pfb_status launch_fft_fast_p(const Plan &plan, LaunchArgs &a, cudaStream_t stream);
 
-// Dispatch on (TT, dtype) for one P; instantiated once per P in its own
-// translation unit (fft_fast_p*.cu) so the build compiles them in parallel.
-template <int P, int TT, int IN>
+// Launch one (P, TT, dtype, NB, packed) instantiation.  Each P is compiled in
+// its own translation unit (fft_fast_p*.cu) so the build runs them in parallel.
+template <int P, int TT, int IN, int NB, bool PK>
 static pfb_status launch_fft_fast_k(LaunchArgs &a, cudaStream_t stream) {
-    auto k = k_fft_fast<P, TT, IN>;
-    constexpr size_t smem = FastCfg<P>::SMEM;
+    using C = FastCfg<P, NB>;
+    auto k = k_fft_fast<P, TT, IN, NB, PK>;
+    constexpr size_t smem = C::SMEM;
     static int grid_cap = 0;  // resident CTAs (computed once per instantiation)
     if (grid_cap == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -184,7 +306,7 @@ static pfb_status launch_fft_fast_k(LaunchArgs &a, cudaStream_t stream) {
         int per_sm = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P / 2, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, smem);
         if (e != cudaSuccess || per_sm < 1) return cuda_fail(e, "occupancy(k_fft_fast)");
         grid_cap = per_sm * sms;
     }
@@ -192,28 +314,39 @@ static pfb_status launch_fft_fast_k(LaunchArgs &a, cudaStream_t stream) {
     if (grid < 1) return PFB_OK;
     a.units_per_cta = (int32_t)((a.nunits + grid - 1) / grid);
     grid = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
-    k<<<(unsigned)grid, P / 2, smem, stream>>>(a);
+    k<<<(unsigned)grid, C::NT, smem, stream>>>(a);
     g_launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch k_fft_fast");
     return PFB_OK;
 }
 
-#define PFB_DEFINE_FFT_FAST_P(PV)                                                              \
-    template <>                                                                                \
-    pfb_status launch_fft_fast_p<PV>(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {   \
-        switch (plan.in_dtype * 100 + plan.TT) {                                               \
-        case PFB_IN_C64 * 100 + 4: return launch_fft_fast_k<PV, 4, PFB_IN_C64>(a, stream);     \
-        case PFB_IN_C64 * 100 + 8: return launch_fft_fast_k<PV, 8, PFB_IN_C64>(a, stream);     \
-        case PFB_IN_C64 * 100 + 16: return launch_fft_fast_k<PV, 16, PFB_IN_C64>(a, stream);   \
-        case PFB_IN_R32 * 100 + 4: return launch_fft_fast_k<PV, 4, PFB_IN_R32>(a, stream);     \
-        case PFB_IN_R32 * 100 + 8: return launch_fft_fast_k<PV, 8, PFB_IN_R32>(a, stream);     \
-        case PFB_IN_R32 * 100 + 16: return launch_fft_fast_k<PV, 16, PFB_IN_R32>(a, stream);   \
-        case PFB_IN_CI8 * 100 + 4: return launch_fft_fast_k<PV, 4, PFB_IN_CI8>(a, stream);     \
-        case PFB_IN_CI8 * 100 + 8: return launch_fft_fast_k<PV, 8, PFB_IN_CI8>(a, stream);     \
-        case PFB_IN_CI8 * 100 + 16: return launch_fft_fast_k<PV, 16, PFB_IN_CI8>(a, stream);   \
-        default: return fail(PFB_ERR_UNSUPPORTED, "fast FFT family: no kernel for this T/dtype"); \
-        }                                                                                      \
+template <int P, int TT, int IN>
+static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t stream) {
+    switch (variant) {
+    case 0: return launch_fft_fast_k<P, TT, IN, 2, false>(a, stream);
+    case 1: return launch_fft_fast_k<P, TT, IN, 2, true>(a, stream);
+    case 2: return launch_fft_fast_k<P, TT, IN, 4, false>(a, stream);
+    default: return launch_fft_fast_k<P, TT, IN, 4, true>(a, stream);
+    }
+}
+
+#define PFB_DEFINE_FFT_FAST_P(PV)                                                                          \
+    template <>                                                                                            \
+    pfb_status launch_fft_fast_p<PV>(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {               \
+        const int v = plan.variant;                                                                        \
+        switch (plan.in_dtype * 100 + plan.TT) {                                                           \
+        case PFB_IN_C64 * 100 + 4: return launch_fft_fast_v<PV, 4, PFB_IN_C64>(v, a, stream);              \
+        case PFB_IN_C64 * 100 + 8: return launch_fft_fast_v<PV, 8, PFB_IN_C64>(v, a, stream);              \
+        case PFB_IN_C64 * 100 + 16: return launch_fft_fast_v<PV, 16, PFB_IN_C64>(v, a, stream);            \
+        case PFB_IN_R32 * 100 + 4: return launch_fft_fast_v<PV, 4, PFB_IN_R32>(v, a, stream);              \
+        case PFB_IN_R32 * 100 + 8: return launch_fft_fast_v<PV, 8, PFB_IN_R32>(v, a, stream);              \
+        case PFB_IN_R32 * 100 + 16: return launch_fft_fast_v<PV, 16, PFB_IN_R32>(v, a, stream);            \
+        case PFB_IN_CI8 * 100 + 4: return launch_fft_fast_v<PV, 4, PFB_IN_CI8>(v, a, stream);              \
+        case PFB_IN_CI8 * 100 + 8: return launch_fft_fast_v<PV, 8, PFB_IN_CI8>(v, a, stream);              \
+        case PFB_IN_CI8 * 100 + 16: return launch_fft_fast_v<PV, 16, PFB_IN_CI8>(v, a, stream);            \
+        default: return fail(PFB_ERR_UNSUPPORTED, "fast FFT family: no kernel for this T/dtype");          \
+        }                                                                                                  \
     }
 
 }  // namespace pfb

@@ -1,9 +1,490 @@
-// Fused polyphase FIR + DFT-matrix product on the tensor cores (split bf16).
+// Fused polyphase FIR + DFT as a product with the Fourier matrix on the
+// tensor cores (tcgen05, sm_103a), split-bf16 with FP32 accumulation.
+//
+// The DFT of Sec. 4.1 (Z = X F) is run in real block form: with the branch
+// sums y[s,p] interleaved (re, im) along K = 2P and the output interleaved
+// along N = 2P,
+//     X[s, 2k+d] = sum_{2p+c} y[s, 2p+c] * B[2p+c, 2k+d]
+//     B[2p,2k] = B[2p+1,2k+1] = cos(th),  B[2p+1,2k] = sin(th),  B[2p,2k+1] = -sin(th)
+// with th = 2 pi (p k mod P) / P.  Both operands are split into bf16 hi + lo
+// (hi = RN(v), lo = RN(v - hi); B from its FP64 value, y from its fp32 value)
+// and three products are accumulated in FP32:  hi*hi + hi*lo + lo*hi.
+//
+// CTA = 5 warps, one CTA per SM (all 512 TMEM columns):
+//   warps 0-3: the FIR of Sec. 5.2 for a 128-spectrum x 32-branch slice per
+//              K block (lane = branch, register window over 32 spectra,
+//              coalesced loads), a warp-local transpose through shared memory
+//              to lane = spectrum, the hi/lo split, tcgen05.st into the A stage
+//              in TMEM; after the K loop, the epilogue (tcgen05.ld -> HBM);
+//   warp 4:    lane 0 bulk-copies the pre-tiled B_hi/B_lo tiles of the K block
+//              into shared memory (mbarrier complete_tx) and issues the
+//              3 x 4 tcgen05.mma (M=128, N=256, K=16, A from TMEM, B from
+//              shared memory, no swizzle) and the tcgen05.commit.
+// Two stages (A in TMEM, B in shared memory) let the FIR of K block g+1 run
+// while the tensor core works on block g.
+// Accumulation is two-level: the tensor core accumulates K2_CHUNK K blocks
+// (3 x 4 x K2_CHUNK MMAs) in TMEM, then the epilogue warps drain the
+// accumulator and add it, in FP32 with round-to-nearest on the CUDA cores,
+// into the output tile (the tile in HBM/L2 is the running sum).  The tensor
+// core's FP32 accumulation adds a small bias per MMA step (about 1.8e-8 of
+// the result per step, measured); chunking bounds it independently of P.  Every mbarrier wait is bounded
+// (1 s of %globaltimer); on expiry the kernel records KERR_TIMEOUT, drains
+// what it issued (bounded) and frees its TMEM.
+#include <cuda_bf16.h>
+
+#include "devutil.cuh"
 #include "internal.h"
 
 namespace pfb {
-int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) { return 0; }
-pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
-    return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path not built yet");
+
+constexpr int K2_M = 128, K2_N = 256, K2_KB = 64;  // reals per tile: M rows, N cols, K block
+constexpr int K2_WARPS = 5, K2_THREADS = K2_WARPS * 32;
+constexpr int K2_TILE_ELEMS = K2_N * K2_KB;  // bf16 elements per B tile (32 KB)
+constexpr int K2_TILE_BYTES = K2_TILE_ELEMS * 2;
+constexpr int K2_SMEM_B = 2 * 2 * K2_TILE_BYTES;  // 2 stages x (hi, lo)
+constexpr int K2_TR = 33;                          // transpose row stride (float2)
+constexpr int K2_SMEM_TR = 4 * 32 * K2_TR * 8;
+constexpr int K2_SMEM_BAR = 64;
+constexpr int K2_SMEM = K2_SMEM_B + K2_SMEM_TR + K2_SMEM_BAR + 1024;  // + alignment slack
+constexpr uint32_t K2_TMEM_COLS = 512;
+constexpr uint32_t K2_COL_A = 256;                 // A stages start after the 256-column accumulator
+constexpr int K2_CHUNK = 8;                        // K blocks per TMEM accumulation chunk
+
+// instruction descriptor, kind::f16: D=f32, A=B=bf16, K-major A and B, N=256, M=128
+constexpr uint32_t K2_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(K2_N >> 3) << 17) |
+                              ((uint32_t)(K2_M >> 4) << 24);
+
+int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) {
+    return ((S + K2_M - 1) / K2_M) * (plan.P / (K2_N / 2));
 }
+
+// ---------------------------------------------------------------------------
+// table: pre-tiled B_hi / B_lo, tile (nt, kb) = 256 (N) x 64 (K) bf16 in the
+// K-major no-swizzle core-matrix order: core matrix (ng, kg) of 8 rows x 8
+// elements at element offset (ng*8 + kg)*64, row r at +8r, element e at +e
+// (leading-dimension byte offset 128 B along K, stride 1024 B along N).
+// ---------------------------------------------------------------------------
+__global__ void gen_dft_bf16x3_kernel(__nv_bfloat16 *Bhi, __nv_bfloat16 *Blo, int P) {
+    const int64_t total = (int64_t)2 * P * 2 * P;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int KBLK = (2 * P) / K2_KB;
+    const int64_t tile = i / K2_TILE_ELEMS;
+    const int w = (int)(i % K2_TILE_ELEMS);
+    const int nt = (int)(tile / KBLK), kb = (int)(tile % KBLK);
+    const int cm = w / 64, within = w % 64;
+    const int ng = cm / 8, kg = cm % 8, r = within / 8, e = within % 8;
+    const int n = nt * K2_N + ng * 8 + r;   // output column 2k + d
+    const int kk = kb * K2_KB + kg * 8 + e; // reduction index 2p + c
+    const int k = n >> 1, dsel = n & 1, p = kk >> 1, csel = kk & 1;
+    const int64_t ex = ((int64_t)p * k) % P;
+    double s, c;
+    sincospi(2.0 * (double)ex / (double)P, &s, &c);
+    double v;
+    if (csel == dsel) v = c;
+    else if (csel == 1) v = s;   // B[2p+1][2k]
+    else v = -s;                 // B[2p][2k+1]
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+    Bhi[i] = hi;
+    Blo[i] = lo;
+}
+
+pfb_status build_gemm_bf16x3_table(Plan &plan) {
+    const int64_t n = (int64_t)2 * plan.P * 2 * plan.P;
+    plan.dft_bytes = 2 * n * sizeof(__nv_bfloat16);
+    PFB_CUDA_TRY(cudaMalloc(&plan.d_dft, plan.dft_bytes));
+    __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(plan.d_dft);
+    gen_dft_bf16x3_kernel<<<(unsigned)((n + 255) / 256), 256>>>(hi, hi + n, plan.P);
+    g_launches++;
+    PFB_CUDA_TRY(cudaGetLastError());
+    return PFB_OK;
+}
+
+pfb_status build_gemm_f32_table(Plan &plan);
+
+pfb_status build_gemm_tables(Plan &plan) {
+    if (plan.family == FAM_GEMM_F32) return build_gemm_f32_table(plan);
+    if (plan.family == FAM_GEMM_BF16X3) {
+        if (plan.P < K2_N / 2 || plan.T > 16) return PFB_OK;  // no kernel; execute reports UNSUPPORTED
+        return build_gemm_bf16x3_table(plan);
+    }
+    return PFB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the completion of the mbarrier phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (globaltimer() - t0 > 1000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    // start address, LBO = 128 B (K direction), SBO = 1024 B (N direction),
+    // version 1 (bit 46), no swizzle
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(accumulate), "r"(K2_IDESC)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(K2_THREADS) : "memory"); }
+
+template <int N>
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_st32<32>(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// Move this thread's accumulator row (256 fp32 columns of TMEM) into the
+// output tile row: first chunk stores, later chunks add (FP32, RN).
+__device__ __forceinline__ void drain_row(uint32_t trow, float *orow, bool valid, bool first, bool last) {
+#pragma unroll 1
+    for (int c = 0; c < K2_N / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(trow + 32 * c, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (valid) {
+            float4 *o = reinterpret_cast<float4 *>(orow + 32 * c);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float4 v = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                       __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                if (!first) {
+                    const float4 prev = o[q];
+                    v.x += prev.x; v.y += prev.y; v.z += prev.z; v.w += prev.w;
+                }
+                if (last) __stcs(o + q, v);
+                else o[q] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel
+// ---------------------------------------------------------------------------
+template <int IN, int TT>
+__global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_constant__ LaunchArgs a, int P) {
+    extern __shared__ __align__(1024) uint8_t k2_smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(k2_smem_raw) + 1023) & ~uintptr_t(1023));
+    float2 *tr_all = reinterpret_cast<float2 *>(sm + K2_SMEM_B);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + K2_SMEM_B + K2_SMEM_TR);  // bfull[0..1], mdone[0..1]
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(bars + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 5);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bfull0 = smem_u32(&bars[0]), mdone0 = smem_u32(&bars[2]);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void *)tmem_slot)),
+                     "r"(K2_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int KBLK = (2 * P) / K2_KB;
+    const int NTL = P / (K2_N / 2);
+    const __nv_bfloat16 *Bhi = static_cast<const __nv_bfloat16 *>(a.aux);
+    const __nv_bfloat16 *Blo = Bhi + (int64_t)NTL * KBLK * K2_TILE_ELEMS;
+    const uint32_t sB = smem_u32(sm);
+
+    uint32_t g = 0;                 // K blocks this CTA has gone through (stage = g & 1)
+    int64_t last_commit = -1;       // last K block whose MMAs were committed (issuer only)
+    int64_t last_copy = -1;         // last K block whose B copies were issued (issuer only)
+    int64_t last_waited_full = -1;  // last K block whose B copies were waited for (issuer only)
+    bool aborted = false;
+
+    for (int64_t u = blockIdx.x; u < a.nunits && !aborted; u += gridDim.x) {
+        const int si = find_stream(a, u);
+        const StreamDesc &d = a.s[si];
+        const int64_t lu = u - d.unit0;
+        const int64_t s0 = (lu / NTL) * K2_M;
+        const int nt = (int)(lu % NTL);
+        for (int kb = 0; kb < KBLK; ++kb, ++g) {
+            const uint32_t stage = g & 1;
+            const bool need_wait = g >= 2;
+            const uint32_t wpar = ((g >> 1) + 1) & 1;  // completion (g-2)/2 of mdone[stage]
+            if (warp == 4) {
+                if (lane == 0) {
+                    if (need_wait && !mbar_wait(mdone0 + 8 * stage, wpar)) {
+                        *abort_flag = 1;
+                    } else {
+                        const uint32_t bf = bfull0 + 8 * stage;
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf),
+                                     "r"(2 * K2_TILE_BYTES)
+                                     : "memory");
+                        const int64_t toff = ((int64_t)nt * KBLK + kb) * K2_TILE_ELEMS;
+                        asm volatile(
+                            "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                sB + stage * 2 * K2_TILE_BYTES),
+                            "l"(Bhi + toff), "r"(K2_TILE_BYTES), "r"(bf)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                sB + stage * 2 * K2_TILE_BYTES + K2_TILE_BYTES),
+                            "l"(Blo + toff), "r"(K2_TILE_BYTES), "r"(bf)
+                            : "memory");
+                        last_copy = g;
+                    }
+                }
+            } else {
+                // ---------------- FIR warps ----------------
+                bool ok = true;
+                if (need_wait) ok = mbar_wait(mdone0 + 8 * stage, wpar);
+                if (!ok) *abort_flag = 1;
+                tc_fence_after();
+                if (ok) {
+                    const int p = kb * 32 + lane;           // this lane's branch
+                    const int64_t f0 = s0 + 32 * warp;      // first frame of the window
+                    float h[TT];
+#pragma unroll
+                    for (int m = 0; m < TT; ++m) h[m] = __ldg(d.taps + m * P + p);
+                    float2 acc[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[j] = make_float2(0.f, 0.f);
+                    const bool interior = f0 >= d.n_state && f0 + 32 + TT - 1 <= d.n_frames;
+                    if (interior) {
+                        const int64_t base = (f0 - d.n_state) * P + p;
+#pragma unroll
+                        for (int i = 0; i < 32 + TT - 1; ++i) {
+                            const float2 v = Loader<IN>::load1(d.in, base + (int64_t)i * P, d.scale);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int m = i - j;
+                                if (m >= 0 && m < TT) {
+                                    acc[j].x = fmaf(h[m], v.x, acc[j].x);
+                                    acc[j].y = fmaf(h[m], v.y, acc[j].y);
+                                }
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32 + TT - 1; ++i) {
+                            const int64_t f = f0 + i;
+                            float2 v = make_float2(0.f, 0.f);
+                            if (f < d.n_frames) {
+                                int64_t smp;
+                                const void *src = frame_source(d, f, P, smp);
+                                v = Loader<IN>::load1(src, smp + p, d.scale);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int m = i - j;
+                                if (m >= 0 && m < TT) {
+                                    acc[j].x = fmaf(h[m], v.x, acc[j].x);
+                                    acc[j].y = fmaf(h[m], v.y, acc[j].y);
+                                }
+                            }
+                        }
+                    }
+                    // transpose: lane = branch -> lane = spectrum row
+                    float2 *tr = tr_all + warp * 32 * K2_TR;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tr[j * K2_TR + lane] = acc[j];
+                    __syncwarp();
+                    uint32_t vh[32], vl[32];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const float2 y = tr[lane * K2_TR + c];
+                        const __nv_bfloat162 hi = __floats2bfloat162_rn(y.x, y.y);
+                        const float2 hf = __bfloat1622float2(hi);
+                        const __nv_bfloat162 lo = __floats2bfloat162_rn(y.x - hf.x, y.y - hf.y);
+                        vh[c] = bf16x2_bits(hi);
+                        vl[c] = bf16x2_bits(lo);
+                    }
+                    __syncwarp();
+                    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+                    const uint32_t acol = K2_COL_A + 64 * stage;
+                    tmem_st32<32>(trow + acol, vh);
+                    tmem_st32<32>(trow + acol + 32, vl);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    if (kb > 0 && kb % K2_CHUNK == 0) {
+                        // chunk boundary: the previous K block's MMAs end the chunk; move the
+                        // accumulator into the output tile before this chunk's first MMA
+                        const uint32_t gp = g - 1;
+                        ok = mbar_wait(mdone0 + 8 * (gp & 1), (gp >> 1) & 1);
+                        if (!ok) *abort_flag = 1;
+                        tc_fence_after();
+                        if (ok) {
+                            const int row = 32 * warp + lane;
+                            const int64_t s = s0 + row;
+                            float *orow = reinterpret_cast<float *>(d.out) + s * 2 * (int64_t)P + (int64_t)nt * K2_N;
+                            drain_row(trow, orow, s < d.S, kb == K2_CHUNK, false);
+                        }
+                    }
+                }
+                tc_fence_before();
+            }
+            named_sync();
+            if (*abort_flag) {
+                aborted = true;
+                break;
+            }
+            if (warp == 4 && lane == 0) {
+                tc_fence_after();
+                if (!mbar_wait(bfull0 + 8 * stage, (g >> 1) & 1)) {
+                    *abort_flag = 1;
+                } else {
+                    last_waited_full = g;
+                    const uint32_t a_hi = tmem + K2_COL_A + 64 * stage, a_lo = a_hi + 32;
+                    const uint32_t b_hi = sB + stage * 2 * K2_TILE_BYTES, b_lo = b_hi + K2_TILE_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < K2_KB / 16; ++ks) {
+                        const uint64_t dh = smem_desc(b_hi + ks * 256), dl = smem_desc(b_lo + ks * 256);
+                        mma_ts(tmem, a_hi + 8 * ks, dh, (kb % K2_CHUNK > 0 || ks > 0) ? 1u : 0u);
+                        mma_ts(tmem, a_hi + 8 * ks, dl, 1u);
+                        mma_ts(tmem, a_lo + 8 * ks, dh, 1u);
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            mdone0 + 8 * stage)
+                        : "memory");
+                    last_commit = g;
+                }
+            }
+        }
+        if (aborted) break;
+        // ---------------- epilogue: accumulator -> HBM ----------------
+        if (warp < 4) {
+            const uint32_t gl = g - 1;
+            bool ok = mbar_wait(mdone0 + 8 * (gl & 1), (gl >> 1) & 1);
+            if (!ok) *abort_flag = 1;
+            tc_fence_after();
+            if (ok) {
+                const int row = 32 * warp + lane;
+                const int64_t s = s0 + row;
+                float *orow = reinterpret_cast<float *>(d.out) + s * 2 * (int64_t)P + (int64_t)nt * K2_N;
+                const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+                drain_row(trow, orow, s < d.S, KBLK <= K2_CHUNK, true);
+            }
+            tc_fence_before();
+        }
+        // all warps: the epilogue's tcgen05.ld are complete before the next
+        // unit's first MMA overwrites the accumulator, and every warp takes
+        // the same abort decision
+        named_sync();
+        if (*abort_flag) aborted = true;
+    }
+
+    // ---------------- teardown ----------------
+    __syncthreads();
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            if (last_commit >= 0) ok = mbar_wait(mdone0 + 8 * (last_commit & 1), (last_commit >> 1) & 1) && ok;
+            if (last_copy > last_waited_full)
+                ok = mbar_wait(bfull0 + 8 * (last_copy & 1), (last_copy >> 1) & 1) && ok;
+            if (!ok || *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
+        }
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(K2_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+template <int IN, int TT>
+static pfb_status launch_k2(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    auto k = k_gemm_bf16x3<IN, TT>;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, K2_SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gemm_bf16x3)");
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = sms;  // one CTA per SM: it takes all 512 TMEM columns
+    }
+    int64_t grid = a.nunits < grid_cap ? a.nunits : grid_cap;
+    if (grid < 1) return PFB_OK;
+    a.units_per_cta = 0;
+    k<<<(unsigned)grid, K2_THREADS, K2_SMEM, stream>>>(a, plan.P);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_gemm_bf16x3");
+    return PFB_OK;
+}
+
+template <int IN>
+static pfb_status launch_k2_t(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    switch (plan.TT) {
+    case 4: return launch_k2<IN, 4>(plan, a, stream);
+    case 8: return launch_k2<IN, 8>(plan, a, stream);
+    default: return launch_k2<IN, 16>(plan, a, stream);
+    }
+}
+
+pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    if (plan.P < K2_N / 2) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs P >= 128");
+    if (plan.T > 16) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs T <= 16");
+    switch (plan.in_dtype) {
+    case PFB_IN_C64: return launch_k2_t<PFB_IN_C64>(plan, a, stream);
+    case PFB_IN_R32: return launch_k2_t<PFB_IN_R32>(plan, a, stream);
+    case PFB_IN_CI8: return launch_k2_t<PFB_IN_CI8>(plan, a, stream);
+    default: return fail(PFB_ERR_INVALID, "bad dtype");
+    }
+}
+
 }  // namespace pfb

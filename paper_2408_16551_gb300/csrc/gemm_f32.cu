@@ -1,10 +1,158 @@
-// Fused polyphase FIR + DFT-matrix product in FP32 on the SIMT cores.
+// Fused polyphase FIR + DFT as a product with the Fourier matrix, FP32 on the
+// SIMT cores (the "plain FP32 form" of the DFT-as-matrix-product, Sec. 4.1:
+// Z(m,n) = sum_l X(m,l) F(l,n) with F = the P x P DFT matrix).
+//
+//   A = y[s, p]      (branch sums, computed in the kernel by the FIR of
+//                     Sec. 5.2 into shared memory; never written to HBM)
+//   B = W[p, k] = exp(-2 pi i (p k mod P) / P)   (complex64, built in FP64)
+//   X[s, k] = sum_p A[s, p] B[p, k]               (complex FMA, FP32 accumulation)
+//
+// Tiling: a work unit is a 64-spectrum x 64-bin output tile; 256 threads,
+// each accumulating a 4 x 4 complex micro-tile (rows ty + 16 i, bins tx + 16 j,
+// conflict-free shared reads, coalesced stores).  The K loop walks 16 branches
+// at a time: the FIR computes the 64 x 16 slice of A, the matching 16 x 64
+// slice of W comes from HBM/L2.  Units are dealt round-robin so CTAs running
+// at the same time share M-tiles (input rows) and W stays hot in L2.
+#include "devutil.cuh"
 #include "internal.h"
 
 namespace pfb {
-int64_t gemm_f32_units(const Plan &plan, int64_t S) { return 0; }
-pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
-    return fail(PFB_ERR_UNSUPPORTED, "FP32 DFT-GEMM path not built yet");
+
+constexpr int G3_BM = 64, G3_BN = 64, G3_BK = 16, G3_THREADS = 256;
+
+int64_t gemm_f32_units(const Plan &plan, int64_t S) {
+    return ((S + G3_BM - 1) / G3_BM) * (plan.P / G3_BN);
 }
-pfb_status build_gemm_tables(Plan &plan) { return PFB_OK; }
+
+// W[p][k] = exp(-2 pi i (p k mod P) / P) in FP64, rounded to complex64
+__global__ void gen_dft_f32_kernel(float2 *W, int P) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * P) return;
+    const int64_t p = i / P, k = i % P;
+    const int64_t e = (p * k) % P;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)P, &s, &c);
+    W[i] = make_float2((float)c, (float)-s);
+}
+
+template <int IN>
+__global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__ LaunchArgs a, int P) {
+    using L = Loader<IN>;
+    __shared__ float2 As[G3_BK][G3_BM + 1];
+    __shared__ float2 Bs[G3_BK][G3_BN];
+    const float2 *W = static_cast<const float2 *>(a.aux);
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int NT = P / G3_BN;
+    for (int64_t u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+        const int si = find_stream(a, u);
+        const StreamDesc &d = a.s[si];
+        const int64_t lu = u - d.unit0;
+        const int64_t s0 = (lu / NT) * G3_BM;
+        const int k0 = (int)(lu % NT) * G3_BN;
+        float2 acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        for (int pc = 0; pc < P; pc += G3_BK) {
+            __syncthreads();
+            // A slice: FIR of 64 spectra x 16 branches (4 per thread)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = t + e * G3_THREADS;
+                const int r = idx >> 4, kk = idx & 15;
+                const int64_t s = s0 + r;
+                const int p = pc + kk;
+                float2 y = make_float2(0.f, 0.f);
+                if (s < d.S) {
+                    for (int m = 0; m < d.T; ++m) {
+                        int64_t smp;
+                        const void *src = frame_source(d, s + m, P, smp);
+                        const float2 v = L::load1(src, smp + p, d.scale);
+                        const float h = __ldg(d.taps + m * P + p);
+                        y.x = fmaf(h, v.x, y.x);
+                        y.y = fmaf(h, v.y, y.y);
+                    }
+                }
+                As[kk][r] = y;
+            }
+            // B slice: 16 x 64 of W
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = t + e * G3_THREADS;
+                const int kk = idx >> 6, c = idx & 63;
+                Bs[kk][c] = __ldg(W + (int64_t)(pc + kk) * P + k0 + c);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < G3_BK; ++kk) {
+                float2 av[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        acc[i][j].x = fmaf(av[i].x, bv[j].x, acc[i][j].x);
+                        acc[i][j].x = fmaf(-av[i].y, bv[j].y, acc[i][j].x);
+                        acc[i][j].y = fmaf(av[i].x, bv[j].y, acc[i][j].y);
+                        acc[i][j].y = fmaf(av[i].y, bv[j].x, acc[i][j].y);
+                    }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t s = s0 + ty + 16 * i;
+            if (s < d.S) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) store_cs(d.out + s * P + k0 + tx + 16 * j, acc[i][j]);
+            }
+        }
+    }
+}
+
+template <int IN>
+static pfb_status launch_g3(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    auto k = k_gemm_f32<IN>;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, G3_THREADS, 0);
+        if (e != cudaSuccess || per_sm < 1) return cuda_fail(e, "occupancy(k_gemm_f32)");
+        grid_cap = sms * per_sm;
+    }
+    int64_t grid = a.nunits < grid_cap ? a.nunits : grid_cap;
+    if (grid < 1) return PFB_OK;
+    a.units_per_cta = 0;
+    k<<<(unsigned)grid, G3_THREADS, 0, stream>>>(a, plan.P);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_gemm_f32");
+    return PFB_OK;
+}
+
+pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    if (plan.P < G3_BN) return fail(PFB_ERR_UNSUPPORTED, "FP32 DFT-GEMM path needs P >= 64");
+    switch (plan.in_dtype) {
+    case PFB_IN_C64: return launch_g3<PFB_IN_C64>(plan, a, stream);
+    case PFB_IN_R32: return launch_g3<PFB_IN_R32>(plan, a, stream);
+    case PFB_IN_CI8: return launch_g3<PFB_IN_CI8>(plan, a, stream);
+    default: return fail(PFB_ERR_INVALID, "bad dtype");
+    }
+}
+
+pfb_status build_gemm_f32_table(Plan &plan) {
+    const int64_t n = (int64_t)plan.P * plan.P;
+    plan.dft_bytes = n * sizeof(float2);
+    PFB_CUDA_TRY(cudaMalloc(&plan.d_dft, plan.dft_bytes));
+    gen_dft_f32_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<float2 *>(plan.d_dft), plan.P);
+    g_launches++;
+    PFB_CUDA_TRY(cudaGetLastError());
+    return PFB_OK;
+}
+
 }  // namespace pfb

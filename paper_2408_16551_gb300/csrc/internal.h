@@ -86,6 +86,7 @@ struct Plan {
     int path = 0;
     int family = 0;
     int esize = 0;                  // bytes per input sample
+    int variant = 0;                // kernel variant (tile shape) within the family
     // device tables (owned)
     double *d_h64 = nullptr;        // FP64 prototype [P*T]
     float *d_taps = nullptr;        // fp32 taps [T][P]
@@ -116,10 +117,13 @@ pfb_status launch_fft_generic(const Plan &plan, LaunchArgs &args, cudaStream_t s
 pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status prepare_family(const Plan &plan);
+const float *family_taps(const Plan &plan);   // tap layout the family's kernels read
 // work units a stream of S spectra contributes to a launch of the plan's family
 int64_t family_units(const Plan &plan, int64_t S);
 bool fft_fast_supported(int P, int T);
 int fft_fast_tt(int T);
+int family_variants(const Plan &plan);        // number of variants the autotuner may pick from
+int default_variant(const Plan &plan);
 
 // Table generators (plan.cu)
 pfb_status build_fft_fast_twiddles(Plan &plan);

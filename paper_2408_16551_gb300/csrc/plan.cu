@@ -168,7 +168,9 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     } else {
         p->family = FAM_GEMM_BF16X3;
     }
-    p->TT = (p->family == FAM_FFT_FAST) ? fft_fast_tt(p->T) : p->T;
+    const bool padded = p->family == FAM_FFT_FAST || (p->family == FAM_GEMM_BF16X3 && p->T <= 16);
+    p->TT = padded ? fft_fast_tt(p->T) : p->T;
+    p->variant = default_variant(*p);
 
     const int P = p->P, T = p->T, L = P * T;
     PFB_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
@@ -182,7 +184,7 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
         g_launches += 2;
     }
     PFB_CUDA_TRY(cudaMalloc(&p->d_taps, sizeof(float) * L));
-    if (p->family == FAM_FFT_FAST) PFB_CUDA_TRY(cudaMalloc(&p->d_taps_pad, sizeof(float) * P * p->TT));
+    if (padded) PFB_CUDA_TRY(cudaMalloc(&p->d_taps_pad, sizeof(float) * P * p->TT));
     int nconv = P * (p->TT > T ? p->TT : T);
     taps_to_f32_kernel<<<(nconv + 255) / 256, 256>>>(p->d_h64, P, T, p->TT, p->d_taps, p->d_taps_pad);
     g_launches++;
@@ -200,9 +202,10 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     }
     PFB_CUDA_TRY(cudaGetLastError());
     PFB_CUDA_TRY(cudaDeviceSynchronize());
-    if (p->family != FAM_GEMM_F32 && p->family != FAM_GEMM_BF16X3) {
+    {
         pfb_status pst = prepare_family(*p);
-        if (pst != PFB_OK) return pst;
+        if (pst != PFB_OK && pst != PFB_ERR_UNSUPPORTED) return pst;
+        clear_error();
     }
     static const char *fam_names[] = {"pfb_fir_fft_f32", "pfb_fir_fft_f32_generic",
                                       "pfb_fir_dftgemm_f32", "pfb_fir_dftgemm_bf16x3"};

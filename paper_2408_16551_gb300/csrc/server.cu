@@ -147,7 +147,7 @@ static pfb_status launch_request(Server &s, Request &r) {
         d.n_state = ps.state_frames;
         d.n_frames = n_frames;
         d.S = r.S;
-        d.taps = plan.family == FAM_FFT_FAST ? plan.d_taps_pad : plan.d_taps;
+        d.taps = family_taps(plan);
         d.scale = plan.desc.in_scale;
         d.T = plan.T;
         pfb_status st = launch_family(plan, &d, 1, cs);

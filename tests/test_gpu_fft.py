@@ -197,3 +197,35 @@ def test_execute_host_matches_device():
     dev = plan.execute(to_device(x)).cpu().numpy()
     host = plan.execute_host(x)
     assert np.array_equal(dev, host)
+
+
+@pytest.mark.parametrize("P,T,dt", [(1024, 16, synth.IN_C64), (512, 8, synth.IN_CI8), (256, 16, synth.IN_R32),
+                                    (128, 4, synth.IN_C64), (64, 12, synth.IN_C64)])
+def test_every_fast_variant_matches_oracle(P, T, dt):
+    import torch
+    n = P * (T - 1 + 8 * 7 + 5) + 3
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=77).generate()
+    ref = reference(x, dt, P, T, synth.WIN_HAMMING)
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_HAMMING)
+    assert plan.num_variants == 4
+    xd = to_device(x)
+    outs = []
+    for v in range(plan.num_variants):
+        plan.variant = v
+        assert plan.variant == v
+        got = plan.execute(xd).cpu().numpy()
+        assert_close(got, ref, what=f"variant {v} P={P} T={T}")
+        outs.append(got)
+
+
+def test_autotune_picks_a_variant_and_keeps_results():
+    P, T = 1024, 16
+    n = P * 4000
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN)
+    ms = plan.autotune(n)
+    assert ms > 0 and 0 <= plan.variant < plan.num_variants
+    x = synth.small_stream(P, T, P * 100, seed=5).generate()
+    got = plan.execute(to_device(x)).cpu().numpy()
+    assert_close(got, reference(x, synth.IN_C64, P, T, synth.WIN_HANN))
+    with pytest.raises(pkg.PFBError):
+        plan.variant = 9

@@ -1,0 +1,114 @@
+"""Parity of the two DFT-as-matrix-product paths with the FP64 oracle:
+FP32 on the SIMT cores (rel. L2 <= 2e-6) and split-bf16 on the tensor cores
+(rel. L2 <= 1e-5), through the C ABI."""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2408_16551_gb300 as pkg
+from paper_2408_16551_gb300 import synth
+
+from gpu_common import TOL_BF16X3, TOL_MAX_BF16X3, assert_close, reference, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_16551_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _run(path, P, T, dt, n, seed=0, window=synth.WIN_HANN):
+    import torch
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=seed, window=window).generate()
+    plan = pkg.Plan(P, T, dt, window, path)
+    X = plan.execute(to_device(x))
+    torch.cuda.synchronize()
+    return plan, x, X.cpu().numpy()
+
+
+@pytest.mark.parametrize("P,T,dt", [(64, 4, synth.IN_C64), (128, 16, synth.IN_R32), (256, 8, synth.IN_CI8),
+                                    (1024, 16, synth.IN_C64), (64, 20, synth.IN_C64)])
+def test_gemm_f32_parity(P, T, dt):
+    n = P * (T - 1 + 64 * 2 + 37) + 5
+    plan, x, got = _run(pkg.PFB_DFT_GEMM_F32, P, T, dt, n, seed=P + T)
+    assert plan.kernel_name == "pfb_fir_dftgemm_f32"
+    assert_close(got, reference(x, dt, P, T, synth.WIN_HANN), what=f"gemm_f32 P={P} T={T}")
+
+
+BF16 = [(128, 16, synth.IN_C64), (256, 8, synth.IN_C64), (256, 4, synth.IN_R32), (512, 16, synth.IN_CI8),
+        (1024, 16, synth.IN_C64), (4096, 16, synth.IN_C64), (256, 3, synth.IN_C64)]
+
+
+@pytest.mark.parametrize("P,T,dt", BF16)
+def test_gemm_bf16x3_parity(P, T, dt):
+    rows = 128 * 2 + 45 if P <= 1024 else 128 + 9
+    n = P * (T - 1 + rows) + 3
+    plan, x, got = _run(pkg.PFB_DFT_GEMM_BF16X3, P, T, dt, n, seed=2 * P + T)
+    assert plan.kernel_name == "pfb_fir_dftgemm_bf16x3"
+    ref = reference(x, dt, P, T, synth.WIN_HANN)
+    e2, em = assert_close(got, ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"bf16x3 P={P} T={T}")
+    assert e2 > 1e-8          # split arithmetic is not exact: the kernel really ran the bf16 path
+
+
+@pytest.mark.parametrize("P,T", [(256, 8), (1024, 16)])
+def test_gemm_bf16x3_matches_split_model(P, T):
+    """Against the FP64 model of the split arithmetic (hi*hi + hi*lo + lo*hi):
+    agreement to FP32-accumulation error separates split error from indexing."""
+    n = P * (T - 1 + 200)
+    plan, x, got = _run(pkg.PFB_DFT_GEMM_BF16X3, P, T, synth.IN_C64, n, seed=9)
+    h = oracle.prototype(P, T, oracle.WIN_HANN)
+    y = oracle.fir(oracle.dequant(x, oracle.IN_C64), P, T, h)
+    model = oracle.split_bf16x3_model(y.astype(np.complex64), P)
+    exact = oracle.dft(y)
+    e_model = oracle.rel_l2(got, model)
+    e_exact = oracle.rel_l2(got, exact)
+    # The tensor core's FP32 accumulation adds ~1.8e-8 of the result per MMA
+    # step; the kernel accumulates chunks of 8 K blocks (96 MMA steps) in TMEM
+    # and sums the chunks in FP32 on the CUDA cores, so the distance to the
+    # exact-split model is bounded near 96 * 1.8e-8 = 1.7e-6 for every P.
+    # An indexing or split bug would show up as an O(1) error here.
+    assert e_model < 3e-6, e_model
+    assert e_exact < 1e-5
+
+
+def test_gemm_bf16x3_deterministic_and_chunked():
+    import torch
+    P, T, chunk = 1024, 16, 1024 * 64
+    x = to_device(synth.small_stream(P, T, chunk * 5, seed=12).generate())
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
+    a = plan.execute(x).clone()
+    b = plan.execute(x)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    srv = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=4)
+    sid = srv.open_stream(plan)
+    outs, tickets = [], []
+    for c in range(5):
+        S = srv.next_spectra(sid, chunk)
+        o = torch.empty((S, P), dtype=torch.complex64, device="cuda")
+        tickets.append(srv.submit(sid, x[c * chunk:(c + 1) * chunk], chunk, o))
+        outs.append(o)
+    for t in tickets:
+        assert srv.wait(t, 20000) == pkg.PFB_OK
+    assert torch.equal(torch.cat(outs), a)
+    srv.close()
+
+
+def test_gemm_paths_report_unsupported_shapes():
+    import torch
+    plan = pkg.Plan(64, 16, path=pkg.PFB_DFT_GEMM_BF16X3)     # P < 128
+    x = torch.zeros(64 * 40, dtype=torch.complex64, device="cuda")
+    with pytest.raises(pkg.PFBError) as ei:
+        plan.execute(x)
+    assert ei.value.status == pkg.PFB_ERR_UNSUPPORTED
+    plan = pkg.Plan(256, 20, path=pkg.PFB_DFT_GEMM_BF16X3)    # T > 16
+    with pytest.raises(pkg.PFBError) as ei:
+        plan.execute(torch.zeros(256 * 40, dtype=torch.complex64, device="cuda"))
+    assert ei.value.status == pkg.PFB_ERR_UNSUPPORTED
