@@ -33,6 +33,39 @@ __device__ __forceinline__ float2 twmul16(float2 b, int m) {
     }
 }
 
+// b * exp(-2 pi i m / 32) for a compile-time m in [0, 16)
+__device__ __forceinline__ float2 twmul32(float2 b, int m) {
+    if ((m & 1) == 0) return twmul16(b, m >> 1);
+    switch (m) {  // cos(pi m/16), sin(pi m/16) for odd m
+    case 1: return cmul(b, make_float2(0.98078528040323043f, -0.19509032201612825f));
+    case 3: return cmul(b, make_float2(0.83146961230254524f, -0.55557023301960218f));
+    case 5: return cmul(b, make_float2(0.55557023301960218f, -0.83146961230254524f));
+    case 7: return cmul(b, make_float2(0.19509032201612825f, -0.98078528040323043f));
+    case 9: return cmul(b, make_float2(-0.19509032201612825f, -0.98078528040323043f));
+    case 11: return cmul(b, make_float2(-0.55557023301960218f, -0.83146961230254524f));
+    case 13: return cmul(b, make_float2(-0.83146961230254524f, -0.55557023301960218f));
+    default: return cmul(b, make_float2(-0.98078528040323043f, -0.19509032201612825f));
+    }
+}
+
+// packed fp32x2 add / sub (Blackwell): one instruction per complex add
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tadd.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tsub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 template <int R>
 __device__ __forceinline__ constexpr int bitrev(int i) {
     int r = 0;
@@ -43,27 +76,39 @@ __device__ __forceinline__ constexpr int bitrev(int i) {
     return r;
 }
 
+// One radix-2 decimation-in-time stage of butterfly span LEN over t[0..R)
+// (twiddle exp(-2 pi i k / LEN) on the odd half), then the next stage.
+template <int R, int LEN, bool PK>
+__device__ __forceinline__ void dit_stages(float2 (&t)[R]) {
+#pragma unroll
+    for (int i = 0; i < R; i += LEN) {
+#pragma unroll
+        for (int k = 0; k < LEN / 2; ++k) {
+            const float2 a = t[i + k];
+            const float2 b = twmul32(t[i + k + LEN / 2], (32 / LEN) * k);
+            if constexpr (PK) {
+                t[i + k] = cadd2(a, b);
+                t[i + k + LEN / 2] = csub2(a, b);
+            } else {
+                t[i + k] = cadd(a, b);
+                t[i + k + LEN / 2] = csub(a, b);
+            }
+        }
+    }
+    if constexpr (LEN * 2 <= R) dit_stages<R, LEN * 2, PK>(t);
+}
+
 // In-register forward DFT, natural order in and out:
-//   v[k] <- sum_r v[r] exp(-2 pi i r k / R),  R in {2, 4, 8, 16}
-// (iterative radix-2 decimation in time over a bit-reversed copy).
-template <int R>
+//   v[k] <- sum_r v[r] exp(-2 pi i r k / R),  R in {2, 4, 8, 16, 32}
+// (iterative radix-2 decimation in time over a bit-reversed copy; PK uses
+// packed fp32x2 adds for the butterflies).  Every index is a compile-time
+// constant, so the arrays live in registers.
+template <int R, bool PK = false>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     float2 t[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) t[i] = v[bitrev<R>(i)];
-#pragma unroll
-    for (int len = 2; len <= R; len <<= 1) {
-#pragma unroll
-        for (int i = 0; i < R; i += len) {
-#pragma unroll
-            for (int k = 0; k < len / 2; ++k) {
-                float2 a = t[i + k];
-                float2 b = twmul16(t[i + k + len / 2], (16 / len) * k);
-                t[i + k] = cadd(a, b);
-                t[i + k + len / 2] = csub(a, b);
-            }
-        }
-    }
+    dit_stages<R, 2, PK>(t);
 #pragma unroll
     for (int i = 0; i < R; ++i) v[i] = t[i];
 }

@@ -27,9 +27,11 @@ pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &a, cudaStream_t stream)
 }  // namespace pfb
 
 namespace pfb {
-// variants: 0 = 2 branches/thread, 1 = same with packed fp32x2 FIR,
-//           2 = 4 branches/thread, 3 = same with packed fp32x2 FIR
-int fast_spectra_per_unit(int variant) { return variant >= 2 ? 4 : 8; }
+// spectra per work unit of each variant (see launch_fft_fast_v)
+int fast_spectra_per_unit(int variant) {
+    static const int sb[] = {8, 8, 4, 4, 16};
+    return sb[variant];
+}
 int64_t fast_units(const Plan &plan, int64_t S) {
     const int sb = fast_spectra_per_unit(plan.variant);
     return (S + sb - 1) / sb;

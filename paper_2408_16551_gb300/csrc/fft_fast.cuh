@@ -33,17 +33,20 @@
 
 namespace pfb {
 
-template <int P, int NB>
+template <int P, int NB, int SB, int MR>
 struct FastCfg {
-    static constexpr int NT = P / NB;
-    static constexpr int SB = 16 / NB;
-    static constexpr int YROW = P + P / 16;
-    static constexpr int NTW = fft_tw_entries(P);
+    static constexpr int NT = P / NB;         // threads
+    static constexpr int V = SB * NB;         // complex values per thread per FFT pass
+    static constexpr int G = MR;              // shared-memory padding: one slot every G entries
+    static constexpr int YROW = P + P / G;
+    static constexpr int NTW = fft_tw_entries(P, MR);
     static constexpr size_t SMEM = (size_t)(SB * YROW + (NTW > 0 ? NTW : 1)) * sizeof(float2);
     static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;
+    static_assert(V % MR == 0 && V >= MR, "a thread carries whole butterflies");
 };
 
-__device__ __forceinline__ int ypad(int i) { return i + (i >> 4); }
+template <int G>
+__device__ __forceinline__ int ypad(int i) { return i + i / G; }
 
 // packed fp32x2 arithmetic (Blackwell): two lanes of fp32 per instruction
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
@@ -94,18 +97,19 @@ __device__ __forceinline__ void load_nb(const void *base, int64_t idx, float s, 
 // ---------------------------------------------------------------------------
 // one Stockham pass
 // ---------------------------------------------------------------------------
-template <int P, int NB, int PASS>
+template <int P, int NB, int SB, int MR, bool PK, int PASS>
 __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float2 *out_row0, int nrows) {
-    using C = FastCfg<P, NB>;
-    constexpr int R = fft_radix(P, PASS);
-    constexpr int NS = fft_ns(P, PASS);
+    using C = FastCfg<P, NB, SB, MR>;
+    constexpr int R = fft_radix(P, PASS, MR);
+    constexpr int NS = fft_ns(P, PASS, MR);
     constexpr int NT = C::NT;
     constexpr int YROW = C::YROW;
-    constexpr bool LAST = (PASS == fft_npasses(P) - 1);
-    constexpr int PER = (C::SB * P / R) / NT;  // butterflies per thread
+    constexpr int G = C::G;
+    constexpr bool LAST = (PASS == fft_npasses(P, MR) - 1);
+    constexpr int PER = (SB * P / R) / NT;  // butterflies per thread
     constexpr int STRIDE = P / R;
-    static_assert(PER * R == 16, "each thread carries 16 values per pass");
-    const float2 *twp = tw + fft_tw_offset(P, PASS);
+    static_assert(PER * R == C::V, "each thread carries V values per pass");
+    const float2 *twp = tw + fft_tw_offset(P, PASS, MR);
     const int t = threadIdx.x;
 
     // butterfly q of this thread: b = t + q*NT -> (row, j); both are a
@@ -126,20 +130,20 @@ __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float
         int row, j;
         rowj(q, row, j);
         const float2 *src = Y + row * YROW;
-        if constexpr (STRIDE % 16 == 0) {
-            src += ypad(j);
+        if constexpr (STRIDE % G == 0) {
+            src += ypad<G>(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = src[r * (STRIDE + STRIDE / 16)];
+            for (int r = 0; r < R; ++r) v[q][r] = src[r * (STRIDE + STRIDE / G)];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = src[ypad(j + r * STRIDE)];
+            for (int r = 0; r < R; ++r) v[q][r] = src[ypad<G>(j + r * STRIDE)];
         }
         if constexpr (NS > 1) {
             const float2 *w = twp + (j % NS) * (R - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], w[r - 1]);
         }
-        dft_reg<R>(v[q]);
+        dft_reg<R, PK>(v[q]);
     }
     if constexpr (!LAST) {
         __syncthreads();
@@ -149,21 +153,21 @@ __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float
             rowj(q, row, j);
             float2 *dst = Y + row * YROW;
             if constexpr (NS == 1) {
-                static_assert(R == 16 || NS > 1, "first pass is radix 16");
-                dst += 17 * j;  // ypad(16 j + r) = 17 j + r
+                static_assert(R == G, "the first pass has the padding radix");
+                dst += (G + 1) * j;  // ypad(G j + r) = (G+1) j + r
 #pragma unroll
                 for (int r = 0; r < R; ++r) dst[r] = v[q][r];
             } else {
-                static_assert(NS % 16 == 0, "Ns is a multiple of 16 after the first pass");
-                dst += ypad((j / NS) * NS * R + (j % NS));
+                static_assert(NS % G == 0, "Ns is a multiple of the padding after the first pass");
+                dst += ypad<G>((j / NS) * NS * R + (j % NS));
 #pragma unroll
-                for (int r = 0; r < R; ++r) dst[r * (NS + NS / 16)] = v[q][r];
+                for (int r = 0; r < R; ++r) dst[r * (NS + NS / G)] = v[q][r];
             }
         }
         __syncthreads();
     } else {
         // NS * R == P: bin index j + r*NS, natural order
-        const bool full = (nrows == C::SB);
+        const bool full = (nrows == SB);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             int row, j;
@@ -177,10 +181,10 @@ __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float
     }
 }
 
-template <int P, int NB, int PASS>
+template <int P, int NB, int SB, int MR, bool PK, int PASS>
 __device__ __forceinline__ void fft_fast_passes(float2 *Y, const float2 *tw, float2 *out_row0, int nrows) {
-    fft_fast_pass<P, NB, PASS>(Y, tw, out_row0, nrows);
-    if constexpr (PASS + 1 < fft_npasses(P)) fft_fast_passes<P, NB, PASS + 1>(Y, tw, out_row0, nrows);
+    fft_fast_pass<P, NB, SB, MR, PK, PASS>(Y, tw, out_row0, nrows);
+    if constexpr (PASS + 1 < fft_npasses(P, MR)) fft_fast_passes<P, NB, SB, MR, PK, PASS + 1>(Y, tw, out_row0, nrows);
 }
 
 // acc[j][b] += h[m][b] * v[b] for the spectra j that frame i feeds
@@ -206,10 +210,10 @@ __device__ __forceinline__ void fir_frame(int i, const float (&h)[TT][NB], const
     }
 }
 
-template <int P, int TT, int IN, int NB, bool PK>
-__global__ void __launch_bounds__(P / NB, FastCfg<P, NB>::MINB) k_fft_fast(const __grid_constant__ LaunchArgs a) {
-    using C = FastCfg<P, NB>;
-    constexpr int NT = C::NT, SB = C::SB, YROW = C::YROW;
+template <int P, int TT, int IN, int NB, int SB, int MR, bool PK>
+__global__ void __launch_bounds__(P / NB, (FastCfg<P, NB, SB, MR>::MINB)) k_fft_fast(const __grid_constant__ LaunchArgs a) {
+    using C = FastCfg<P, NB, SB, MR>;
+    constexpr int NT = C::NT, YROW = C::YROW;
     constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
     constexpr bool REAL = (IN == PFB_IN_R32);
     extern __shared__ __align__(16) float2 sm[];
@@ -278,26 +282,26 @@ __global__ void __launch_bounds__(P / NB, FastCfg<P, NB>::MINB) k_fft_fast(const
             }
         }
         __syncthreads();  // previous unit's last pass has finished reading Y
-        const int c = ypad(q0);
+        const int c = ypad<C::G>(q0);
 #pragma unroll
         for (int j = 0; j < SB; ++j)
 #pragma unroll
             for (int b = 0; b < NB; ++b) Y[j * YROW + c + b] = acc[j][b];
         __syncthreads();
         // ---- P-point FFT of the SB rows, last pass stores to HBM ----
-        fft_fast_passes<P, NB, 0>(Y, tw, d.out + s0 * P, nrows);
+        fft_fast_passes<P, NB, SB, MR, PK, 0>(Y, tw, d.out + s0 * P, nrows);
     }
 }
 
 template <int P>
 pfb_status launch_fft_fast_p(const Plan &plan, LaunchArgs &a, cudaStream_t stream);
 
-// Launch one (P, TT, dtype, NB, packed) instantiation.  Each P is compiled in
-// its own translation unit (fft_fast_p*.cu) so the build runs them in parallel.
-template <int P, int TT, int IN, int NB, bool PK>
+// Launch one instantiation.  Each P is compiled in its own translation unit
+// (fft_fast_p*.cu) so the build runs them in parallel.
+template <int P, int TT, int IN, int NB, int SB, int MR, bool PK>
 static pfb_status launch_fft_fast_k(LaunchArgs &a, cudaStream_t stream) {
-    using C = FastCfg<P, NB>;
-    auto k = k_fft_fast<P, TT, IN, NB, PK>;
+    using C = FastCfg<P, NB, SB, MR>;
+    auto k = k_fft_fast<P, TT, IN, NB, SB, MR, PK>;
     constexpr size_t smem = C::SMEM;
     static int grid_cap = 0;  // resident CTAs (computed once per instantiation)
     if (grid_cap == 0) {
@@ -321,13 +325,20 @@ static pfb_status launch_fft_fast_k(LaunchArgs &a, cudaStream_t stream) {
     return PFB_OK;
 }
 
+// variants (tile shapes the autotuner chooses from):
+//   0: 2 branches/thread,  8 spectra/unit, radix 16, scalar fp32
+//   1: 2 branches/thread,  8 spectra/unit, radix 16, packed fp32x2
+//   2: 4 branches/thread,  4 spectra/unit, radix 16, scalar fp32
+//   3: 4 branches/thread,  4 spectra/unit, radix 16, packed fp32x2
+//   4: 2 branches/thread, 16 spectra/unit, radix 32, packed fp32x2
 template <int P, int TT, int IN>
 static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t stream) {
     switch (variant) {
-    case 0: return launch_fft_fast_k<P, TT, IN, 2, false>(a, stream);
-    case 1: return launch_fft_fast_k<P, TT, IN, 2, true>(a, stream);
-    case 2: return launch_fft_fast_k<P, TT, IN, 4, false>(a, stream);
-    default: return launch_fft_fast_k<P, TT, IN, 4, true>(a, stream);
+    case 0: return launch_fft_fast_k<P, TT, IN, 2, 8, 16, false>(a, stream);
+    case 1: return launch_fft_fast_k<P, TT, IN, 2, 8, 16, true>(a, stream);
+    case 2: return launch_fft_fast_k<P, TT, IN, 4, 4, 16, false>(a, stream);
+    case 3: return launch_fft_fast_k<P, TT, IN, 4, 4, 16, true>(a, stream);
+    default: return launch_fft_fast_k<P, TT, IN, 2, 16, 32, true>(a, stream);
     }
 }
 
@@ -335,6 +346,7 @@ static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t str
     template <>                                                                                            \
     pfb_status launch_fft_fast_p<PV>(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {               \
         const int v = plan.variant;                                                                        \
+        a.tw = (v >= 4) ? plan.d_tw32 : plan.d_tw;                                                         \
         switch (plan.in_dtype * 100 + plan.TT) {                                                           \
         case PFB_IN_C64 * 100 + 4: return launch_fft_fast_v<PV, 4, PFB_IN_C64>(v, a, stream);              \
         case PFB_IN_C64 * 100 + 8: return launch_fft_fast_v<PV, 8, PFB_IN_C64>(v, a, stream);              \

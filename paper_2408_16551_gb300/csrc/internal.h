@@ -91,7 +91,8 @@ struct Plan {
     double *d_h64 = nullptr;        // FP64 prototype [P*T]
     float *d_taps = nullptr;        // fp32 taps [T][P]
     float *d_taps_pad = nullptr;    // fp32 taps front-padded [TT][P] (fast FFT family)
-    float2 *d_tw = nullptr;         // FFT twiddles (layout per family)
+    float2 *d_tw = nullptr;         // FFT twiddles (layout per family; radix-16 pass list)
+    float2 *d_tw32 = nullptr;       // radix-32 pass list twiddles (fast FFT family)
     float2 *d_tw_r2 = nullptr;      // radix-2 table w^r, r < P/2 (generic family)
     void *d_dft = nullptr;          // DFT matrix (GEMM families)
     size_t dft_bytes = 0;

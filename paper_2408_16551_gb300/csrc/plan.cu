@@ -98,19 +98,25 @@ __global__ void gen_tw_pass_kernel(float2 *tw, int Ns, int R) {
 // ---------------------------------------------------------------------------
 // fast-FFT family twiddles (pass list in fftplan.h)
 // ---------------------------------------------------------------------------
-pfb_status build_fft_fast_twiddles(Plan &plan) {
-    const int P = plan.P;
-    int total = fft_tw_entries(P);
-    PFB_CUDA_TRY(cudaMalloc(&plan.d_tw, (total > 0 ? total : 1) * sizeof(float2)));
-    for (int i = 0; i < fft_npasses(P); ++i) {
-        int Ns = fft_ns(P, i), R = fft_radix(P, i);
+static pfb_status build_pass_table(int P, int MR, float2 **out) {
+    const int total = fft_tw_entries(P, MR);
+    PFB_CUDA_TRY(cudaMalloc(out, (total > 0 ? total : 1) * sizeof(float2)));
+    for (int i = 0; i < fft_npasses(P, MR); ++i) {
+        const int Ns = fft_ns(P, i, MR), R = fft_radix(P, i, MR);
         if (Ns == 1) continue;
-        int n = Ns * (R - 1);
-        gen_tw_pass_kernel<<<(n + 255) / 256, 256>>>(plan.d_tw + fft_tw_offset(P, i), Ns, R);
+        const int n = Ns * (R - 1);
+        gen_tw_pass_kernel<<<(n + 255) / 256, 256>>>(*out + fft_tw_offset(P, i, MR), Ns, R);
         g_launches++;
     }
     PFB_CUDA_TRY(cudaGetLastError());
     return PFB_OK;
+}
+
+// tables for the radix-16 and radix-32 pass lists (variants pick one)
+pfb_status build_fft_fast_twiddles(Plan &plan) {
+    pfb_status st = build_pass_table(plan.P, 16, &plan.d_tw);
+    if (st != PFB_OK) return st;
+    return build_pass_table(plan.P, 32, &plan.d_tw32);
 }
 
 // ---------------------------------------------------------------------------
@@ -145,6 +151,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->d_taps_pad);
     cudaFree(p->d_tw);
     cudaFree(p->d_tw_r2);
+    cudaFree(p->d_tw32);
     cudaFree(p->d_dft);
     cudaFree(p->d_err);
     cudaFree(p->d_stage_in);

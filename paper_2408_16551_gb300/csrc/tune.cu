@@ -75,7 +75,7 @@ static void save_file_cache() {
     std::rename((std::string(path) + ".tmp").c_str(), path);
 }
 
-int family_variants(const Plan &plan) { return plan.family == FAM_FFT_FAST ? 4 : 1; }
+int family_variants(const Plan &plan) { return plan.family == FAM_FFT_FAST ? 5 : 1; }
 
 int default_variant(const Plan &plan) {
     if (family_variants(plan) <= 1) return 0;
@@ -87,8 +87,9 @@ int default_variant(const Plan &plan) {
         int x = std::atoi(v);
         if (x >= 0 && x < family_variants(plan)) return x;
     }
-    // built-in choice: packed fp32x2 FIR, 4 branches/thread for P >= 512
-    return plan.P >= 512 ? 3 : 1;
+    // built-in choice (fastest in a GB300 sweep over P = 64..1024, T = 16):
+    // 2 branches per thread, 8 spectra per unit, radix 16, scalar fp32
+    return 0;
 }
 
 }  // namespace pfb

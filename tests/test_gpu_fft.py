@@ -207,7 +207,7 @@ def test_every_fast_variant_matches_oracle(P, T, dt):
     x = synth.small_stream(P, T, n, in_dtype=dt, seed=77).generate()
     ref = reference(x, dt, P, T, synth.WIN_HAMMING)
     plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_HAMMING)
-    assert plan.num_variants == 4
+    assert plan.num_variants == 5
     xd = to_device(x)
     outs = []
     for v in range(plan.num_variants):
