@@ -28,6 +28,7 @@ int64_t generic_units(int P, int64_t S);
 int64_t fast_units(const Plan &plan, int64_t S);
 int64_t gemm_f32_units(const Plan &plan, int64_t S);
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S);
+int64_t cluster_units(int64_t S);
 
 int64_t family_units(const Plan &plan, int64_t S) {
     switch (plan.family) {
@@ -35,6 +36,7 @@ int64_t family_units(const Plan &plan, int64_t S) {
     case FAM_FFT_GENERIC: return generic_units(plan.P, S);
     case FAM_GEMM_F32: return gemm_f32_units(plan, S);
     case FAM_GEMM_BF16X3: return gemm_bf16x3_units(plan, S);
+    case FAM_FFT_CLUSTER: return cluster_units(S);
     default: return 0;
     }
 }
@@ -69,6 +71,7 @@ pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_
         case FAM_FFT_GENERIC: st = launch_fft_generic(plan, a, stream); break;
         case FAM_GEMM_F32: st = launch_gemm_f32(plan, a, stream); break;
         case FAM_GEMM_BF16X3: st = launch_gemm_bf16x3(plan, a, stream); break;
+        case FAM_FFT_CLUSTER: st = launch_fft_cluster(plan, a, stream); break;
         default: st = fail(PFB_ERR_INTERNAL, "unknown kernel family");
         }
         if (st != PFB_OK) return st;
@@ -86,6 +89,7 @@ pfb_status prepare_family(const Plan &plan) {
     case FAM_FFT_GENERIC: return launch_fft_generic(plan, a, nullptr);
     case FAM_GEMM_F32: return launch_gemm_f32(plan, a, nullptr);
     case FAM_GEMM_BF16X3: return launch_gemm_bf16x3(plan, a, nullptr);
+    case FAM_FFT_CLUSTER: return launch_fft_cluster(plan, a, nullptr);
     default: return PFB_OK;
     }
 }

@@ -1,0 +1,75 @@
+// Launcher of the cluster FFT family (P = 2048, 4096; kernels in fft_cluster.cuh).
+#include "fft_cluster.cuh"
+
+namespace pfb {
+
+int64_t cluster_units(int64_t S) { return (S + 7) / 8; }
+
+template <int CS, int TT, int IN>
+static pfb_status launch_cluster_k(LaunchArgs &a, cudaStream_t stream) {
+    using C = ClusterCfg<CS>;
+    auto k = k_fft_cluster<CS, TT, IN>;
+    static int cap_clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::NT, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cap_clusters == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fft_cluster)");
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cfg.gridDim = dim3((unsigned)(sms / CS * CS), 1, 1);
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess || n < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                                                        "cudaOccupancyMaxActiveClusters(k_fft_cluster)");
+        cap_clusters = n;
+    }
+    int64_t clusters = a.nunits < cap_clusters ? a.nunits : cap_clusters;
+    if (clusters < 1) return PFB_OK;
+    a.units_per_cta = (int32_t)((a.nunits + clusters - 1) / clusters);
+    clusters = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
+    cfg.gridDim = dim3((unsigned)(clusters * CS), 1, 1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
+    g_launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_fft_cluster");
+    return PFB_OK;
+}
+
+template <int CS>
+static pfb_status launch_cluster_cs(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    switch (plan.in_dtype * 100 + plan.TT) {
+    case PFB_IN_C64 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_C64>(a, stream);
+    case PFB_IN_C64 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_C64>(a, stream);
+    case PFB_IN_C64 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_C64>(a, stream);
+    case PFB_IN_R32 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_R32>(a, stream);
+    case PFB_IN_R32 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_R32>(a, stream);
+    case PFB_IN_R32 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_R32>(a, stream);
+    case PFB_IN_CI8 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_CI8>(a, stream);
+    case PFB_IN_CI8 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_CI8>(a, stream);
+    case PFB_IN_CI8 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_CI8>(a, stream);
+    default: return fail(PFB_ERR_UNSUPPORTED, "cluster FFT family: no kernel for this T/dtype");
+    }
+}
+
+bool fft_cluster_supported(int P, int T) { return (P == 2048 || P == 4096) && T >= 1 && T <= 16; }
+
+pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    a.aux = plan.d_tw_r2;
+    switch (plan.P) {
+    case 2048: return launch_cluster_cs<2>(plan, a, stream);
+    case 4096: return launch_cluster_cs<4>(plan, a, stream);
+    default: return fail(PFB_ERR_UNSUPPORTED, "cluster FFT family: P must be 2048 or 4096");
+    }
+}
+
+}  // namespace pfb

@@ -29,7 +29,7 @@ pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &a, cudaStream_t stream)
 namespace pfb {
 // spectra per work unit of each variant (see launch_fft_fast_v)
 int fast_spectra_per_unit(int variant) {
-    static const int sb[] = {8, 8, 4, 4, 16};
+    static const int sb[] = {8, 8, 4, 4, 16, 1};
     return sb[variant];
 }
 int64_t fast_units(const Plan &plan, int64_t S) {

@@ -33,18 +33,6 @@
 
 namespace pfb {
 
-template <int P, int NB, int SB, int MR>
-struct FastCfg {
-    static constexpr int NT = P / NB;         // threads
-    static constexpr int V = SB * NB;         // complex values per thread per FFT pass
-    static constexpr int G = MR;              // shared-memory padding: one slot every G entries
-    static constexpr int YROW = P + P / G;
-    static constexpr int NTW = fft_tw_entries(P, MR);
-    static constexpr size_t SMEM = (size_t)(SB * YROW + (NTW > 0 ? NTW : 1)) * sizeof(float2);
-    static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;
-    static_assert(V % MR == 0 && V >= MR, "a thread carries whole butterflies");
-};
-
 template <int G>
 __device__ __forceinline__ int ypad(int i) { return i + i / G; }
 
@@ -57,6 +45,24 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
     return d;
 }
+
+}  // namespace pfb
+
+#include "fft_ws.cuh"
+
+namespace pfb {
+
+template <int P, int NB, int SB, int MR>
+struct FastCfg {
+    static constexpr int NT = P / NB;         // threads
+    static constexpr int V = SB * NB;         // complex values per thread per FFT pass
+    static constexpr int G = MR;              // shared-memory padding: one slot every G entries
+    static constexpr int YROW = P + P / G;
+    static constexpr int NTW = fft_tw_entries(P, MR);
+    static constexpr size_t SMEM = (size_t)(SB * YROW + (NTW > 0 ? NTW : 1)) * sizeof(float2);
+    static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;
+    static_assert(V % MR == 0 && V >= MR, "a thread carries whole butterflies");
+};
 
 // ---------------------------------------------------------------------------
 // loads of NB consecutive branches of one frame
@@ -331,6 +337,8 @@ static pfb_status launch_fft_fast_k(LaunchArgs &a, cudaStream_t stream) {
 //   2: 4 branches/thread,  4 spectra/unit, radix 16, scalar fp32
 //   3: 4 branches/thread,  4 spectra/unit, radix 16, packed fp32x2
 //   4: 2 branches/thread, 16 spectra/unit, radix 32, packed fp32x2
+//   5: warp-specialised, TMA-fed ring, streaming FIR state (fft_ws.cuh);
+//      P >= 128 and T equal to the compiled tap count
 template <int P, int TT, int IN>
 static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t stream) {
     switch (variant) {
@@ -338,7 +346,15 @@ static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t str
     case 1: return launch_fft_fast_k<P, TT, IN, 2, 8, 16, true>(a, stream);
     case 2: return launch_fft_fast_k<P, TT, IN, 4, 4, 16, false>(a, stream);
     case 3: return launch_fft_fast_k<P, TT, IN, 4, 4, 16, true>(a, stream);
-    default: return launch_fft_fast_k<P, TT, IN, 2, 16, 32, true>(a, stream);
+    case 4: return launch_fft_fast_k<P, TT, IN, 2, 16, 32, true>(a, stream);
+    default:
+        if constexpr (P >= 128) {
+            for (int i = 0; i < a.nstreams; ++i)
+                if (a.s[i].T != TT) return fail(PFB_ERR_UNSUPPORTED, "variant 5 needs T in {4, 8, 16}");
+            return launch_fft_ws_k<P, TT, IN>(a, stream);
+        } else {
+            return fail(PFB_ERR_UNSUPPORTED, "variant 5 needs P >= 128");
+        }
     }
 }
 
@@ -346,7 +362,7 @@ static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t str
     template <>                                                                                            \
     pfb_status launch_fft_fast_p<PV>(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {               \
         const int v = plan.variant;                                                                        \
-        a.tw = (v >= 4) ? plan.d_tw32 : plan.d_tw;                                                         \
+        a.tw = (v == 4) ? plan.d_tw32 : plan.d_tw;                                                         \
         switch (plan.in_dtype * 100 + plan.TT) {                                                           \
         case PFB_IN_C64 * 100 + 4: return launch_fft_fast_v<PV, 4, PFB_IN_C64>(v, a, stream);              \
         case PFB_IN_C64 * 100 + 8: return launch_fft_fast_v<PV, 8, PFB_IN_C64>(v, a, stream);              \

@@ -1,0 +1,406 @@
+// Fused polyphase FIR + FFT, FP32, warp-specialised and fed by the TMA engine
+// (variant 5 of the fast FFT family).
+//
+//   y[s,p] = sum_{m<T} h[m*P+p] * x[(s+m)*P+p]     (Sec. 5.2 per-branch FIR,
+//                                                    Sec. 4.3 correlation form)
+//   X[s,k] = sum_p y[s,p] exp(-2 pi i p k / P)       (Sec. 4.1, the DFT)
+//
+// One CTA per SM walks a contiguous range of spectra.  Its warps have roles:
+//   producer (1 warp, lane 0): 1-D bulk copies of whole input frames into a
+//       ring of NSLOT shared-memory slots (mbarrier complete_tx), in frame
+//       order, so every input byte is read from HBM exactly once per CTA;
+//   FIR warps (P/NB threads, NB consecutive branches each): stream the frames
+//       out of the ring; the branch sums of the T spectra a frame feeds live in
+//       registers (slot (s mod T), rotated at compile time by unrolling the
+//       frame loop T times), so each frame costs T fp32x2 FMAs per branch and
+//       one spectrum of branch sums completes per frame; rows go to a
+//       double-buffered batch buffer Y in shared memory (SB spectra);
+//   FFT warps (96 threads): radix-16 Stockham passes, out of place
+//       (Y -> W0 -> W1 -> HBM), natural-order bins stored straight from
+//       registers; they release Y as soon as the first pass has read it.
+// Roles hand over through mbarriers; every wait is bounded (1 s of
+// %globaltimer) and a timeout sets the launch's error word and winds down.
+// For P = 1024 (4 branches per FIR thread, 16 taps) the FIR warpgroups take
+// 208 registers, the FFT warpgroup 72 and the producer warpgroup 24
+// (setmaxnreg): 256*208 + 128*72 + 128*24 = 512*128 registers at launch.
+#pragma once
+
+#include "devutil.cuh"
+#include "fftplan.h"
+#include "internal.h"
+#include "sync.cuh"
+
+namespace pfb {
+
+template <int P, int TT, int IN>
+struct WsCfg {
+    static constexpr int NB = P >= 1024 ? 4 : (P >= 512 ? 2 : 1);  // branches per FIR thread
+    static constexpr int NFT = P / NB;                               // FIR threads
+    static constexpr int NFIRW = NFT / 32;
+    static constexpr bool SETMAXNREG = (P >= 1024);
+    static constexpr int NFFTW = 4;                                  // FFT warps (one per SM sub-partition)
+    static constexpr int NFFTT = NFFTW * 32;
+    static constexpr int PRODW = NFIRW + NFFTW;                      // producer warp index
+    // with setmaxnreg the producer sits in a warpgroup of its own (3 idle warps)
+    static constexpr int NTHREADS = NFT + NFFTT + (SETMAXNREG ? 128 : 32);
+    static constexpr int SB = 4;                                     // spectra per FFT batch
+    static constexpr int MR = 16;
+    static constexpr int G = 16;
+    static constexpr int YROW = P + P / G;
+    static constexpr int NSLOT = 8;
+    static constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
+    static constexpr int FB = P * ESZ;                               // frame bytes
+    static constexpr int NTW = fft_tw_entries(P, MR);
+    static constexpr int NPASS = fft_npasses(P, MR);
+    // shared memory layout (bytes)
+    static constexpr int OFF_RING = 0;
+    static constexpr int OFF_Y = OFF_RING + NSLOT * FB;
+    static constexpr int YBUF = SB * YROW * 8;
+    static constexpr int OFF_W = OFF_Y + 2 * YBUF;
+    static constexpr int OFF_TW = OFF_W + 2 * YBUF;
+    static constexpr int OFF_META = OFF_TW + (NTW > 0 ? NTW : 1) * 8;
+    static constexpr int OFF_BAR = OFF_META + 3 * 32;
+    static constexpr int NBAR = 2 * NSLOT + 4;
+    static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
+    static_assert(NFT % 128 == 0 || !SETMAXNREG, "FIR warps form whole warpgroups");
+    static_assert(NFIRW * 32 + NFFTT + (SETMAXNREG ? 128 : 32) == NTHREADS, "layout");
+    // register split (setmaxnreg): FIR 208, FFT 72, producer warpgroup 24
+    static_assert(!SETMAXNREG || NFT * 208 + NFFTT * 72 + 128 * 24 <= NTHREADS * (65536 / NTHREADS), "registers");
+};
+
+struct WsMeta {
+    float2 *out;   // first output row of the batch
+    int nrows;
+    int pad[5];
+};
+
+// one out-of-place Stockham pass over a batch of SB rows, run by the FFT warps
+template <int P, int MR, int SB, int PASS, bool LAST, int YROW, int G>
+__device__ __forceinline__ void ws_pass(const float2 *src, float2 *dst, const float2 *tw, float2 *out_row0, int nrows,
+                                        int ft, int nft) {
+    constexpr int R = fft_radix(P, PASS, MR);
+    constexpr int NS = fft_ns(P, PASS, MR);
+    constexpr int STRIDE = P / R;
+    constexpr int NBF = SB * STRIDE;  // butterflies in the batch
+    const float2 *twp = tw + fft_tw_offset(P, PASS, MR);
+#pragma unroll 1
+    for (int b = ft; b < NBF; b += nft) {
+        const int row = b / STRIDE, j = b % STRIDE;
+        float2 v[R];
+        const float2 *s = src + row * YROW;
+        if constexpr (STRIDE % G == 0) {
+            s += ypad<G>(j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[r * (STRIDE + STRIDE / G)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[ypad<G>(j + r * STRIDE)];
+        }
+        if constexpr (NS > 1) {
+            const float2 *w = twp + (j % NS) * (R - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
+        }
+        dft_reg<R, true>(v);
+        if constexpr (!LAST) {
+            float2 *d = dst + row * YROW;
+            if constexpr (NS == 1) {
+                static_assert(R == G, "first pass radix equals the padding period");
+                d += (G + 1) * j;
+#pragma unroll
+                for (int r = 0; r < R; ++r) d[r] = v[r];
+            } else {
+                d += ypad<G>((j / NS) * NS * R + (j % NS));
+#pragma unroll
+                for (int r = 0; r < R; ++r) d[r * (NS + NS / G)] = v[r];
+            }
+        } else {
+            if (row < nrows) {
+                float2 *o = out_row0 + row * P + j;
+#pragma unroll
+                for (int r = 0; r < R; ++r) store_cs(o + r * NS, v[r]);
+            }
+        }
+    }
+}
+
+template <int P, int MR, int SB, int PASS, int YROW, int G>
+__device__ __forceinline__ void ws_passes(float2 *Y, float2 *W0, float2 *W1, const float2 *tw, float2 *out_row0,
+                                          int nrows, int ft, int nft, uint32_t yempty_bar, int nfftt) {
+    constexpr int NPASS = fft_npasses(P, MR);
+    constexpr bool LAST = (PASS == NPASS - 1);
+    const float2 *src = (PASS == 0) ? Y : ((PASS % 2 == 1) ? W0 : W1);
+    float2 *dst = (PASS % 2 == 0) ? W0 : W1;
+    ws_pass<P, MR, SB, PASS, LAST, YROW, G>(src, dst, tw, out_row0, nrows, ft, nft);
+    if constexpr (!LAST) {
+        named_bar_sync<1>(nfftt);
+        if (PASS == 0 && ft == 0) mbar_arrive(yempty_bar);  // Y has been read: the FIR warps may refill it
+        ws_passes<P, MR, SB, PASS + 1, YROW, G>(Y, W0, W1, tw, out_row0, nrows, ft, nft, yempty_bar, nfftt);
+    } else if constexpr (PASS == 0) {
+        // single-pass transform (not used for P >= 64)
+        if (ft == 0) mbar_arrive(yempty_bar);
+    }
+}
+
+// iterate the CTA's spectra range as (stream, [sA, sB)) segments
+struct WsRange {
+    int64_t u, u1;
+};
+
+__device__ __forceinline__ bool ws_next_segment(const LaunchArgs &a, WsRange &r, int &si, int64_t &sA, int64_t &sB) {
+    if (r.u >= r.u1) return false;
+    si = find_stream(a, r.u);
+    const StreamDesc &d = a.s[si];
+    const int64_t end = min(r.u1, d.unit0 + d.S);
+    sA = r.u - d.unit0;
+    sB = end - d.unit0;
+    r.u = end;
+    return true;
+}
+
+template <int P, int TT, int IN>
+__global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const __grid_constant__ LaunchArgs a) {
+    using C = WsCfg<P, TT, IN>;
+    constexpr int NB = C::NB, SB = C::SB, NSLOT = C::NSLOT, YROW = C::YROW, G = C::G;
+    extern __shared__ __align__(128) uint8_t ws_smem[];
+    uint8_t *ring = ws_smem + C::OFF_RING;
+    float2 *Y = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y);
+    float2 *W = reinterpret_cast<float2 *>(ws_smem + C::OFF_W);
+    float2 *tw = reinterpret_cast<float2 *>(ws_smem + C::OFF_TW);
+    WsMeta *meta = reinterpret_cast<WsMeta *>(ws_smem + C::OFF_META);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ws_smem + C::OFF_BAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + C::NBAR);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[NSLOT]);
+    const uint32_t yfull0 = smem_u32(&bars[2 * NSLOT]), yempty0 = smem_u32(&bars[2 * NSLOT + 2]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSLOT; ++i) {
+            mbar_init(full0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, C::NFIRW);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(yfull0 + 8 * i, C::NFIRW);
+            mbar_init(yempty0 + 8 * i, 1);
+        }
+        mbar_init_fence();
+        *abort_flag = 0;
+    }
+    __syncthreads();
+
+    WsRange range;
+    range.u = (int64_t)blockIdx.x * a.units_per_cta;
+    range.u1 = min(range.u + (int64_t)a.units_per_cta, a.nunits);
+
+    if (warp < C::NFIRW) {
+        // ======================= FIR warps =======================
+        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
+        const int t = threadIdx.x;
+        const int q0 = NB * t;
+        float h[TT][NB];
+        float2 pend[TT][NB];
+        int cur = -1;
+        uint32_t pc = 0;   // frames consumed
+        uint32_t bc = 0;   // batches produced
+        int brow = 0;      // rows written into the current batch
+        bool ok = true;
+        int si;
+        int64_t sA, sB;
+        while (ok && ws_next_segment(a, range, si, sA, sB)) {
+            const StreamDesc &d = a.s[si];
+            if (si != cur) {
+                cur = si;
+#pragma unroll
+                for (int m = 0; m < TT; ++m)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) h[m][b] = __ldg(d.taps + m * P + q0 + b);
+            }
+            const int64_t nspec = sB - sA;
+            const int64_t nfr = nspec + TT - 1;
+            float2 *out_seg = d.out + sA * P;
+            int64_t first_row_spec = 0;  // segment-relative spectrum of the batch's first row
+            for (int64_t i0 = 0; i0 < nfr && ok; i0 += TT) {
+#pragma unroll
+                for (int k = 0; k < TT; ++k) {
+                    const int64_t i = i0 + k;
+                    if (i < nfr && ok) {
+                        // ---- frame i of the segment from the ring ----
+                        const uint32_t slot = pc % NSLOT;
+                        // warp-uniform decision: every lane takes the same path
+                        if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * slot, (pc / NSLOT) & 1))) {
+                            *abort_flag = 1;
+                            ok = false;
+                        }
+                        float2 v[NB];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) v[b] = make_float2(0.f, 0.f);
+                        if (ok) {
+                            const uint8_t *fr = ring + slot * C::FB;
+                            float sc = d.scale;
+                            if constexpr (IN == PFB_IN_C64) {
+                                const float4 *p4 = reinterpret_cast<const float4 *>(fr) + (q0 >> 1);
+#pragma unroll
+                                for (int b2 = 0; b2 < (NB + 1) / 2; ++b2) {
+                                    if (NB == 1) {
+                                        v[0] = reinterpret_cast<const float2 *>(fr)[q0];
+                                    } else {
+                                        const float4 w4 = p4[b2];
+                                        v[2 * b2] = make_float2(w4.x, w4.y);
+                                        v[2 * b2 + 1] = make_float2(w4.z, w4.w);
+                                    }
+                                }
+                            } else if constexpr (IN == PFB_IN_R32) {
+                                const float *pf = reinterpret_cast<const float *>(fr) + q0;
+#pragma unroll
+                                for (int b = 0; b < NB; ++b) v[b] = make_float2(pf[b], 0.f);
+                            } else {
+                                const char2 *pc2 = reinterpret_cast<const char2 *>(fr) + q0;
+#pragma unroll
+                                for (int b = 0; b < NB; ++b) {
+                                    const char2 c2 = pc2[b];
+                                    v[b] = make_float2((float)c2.x * sc, (float)c2.y * sc);
+                                }
+                            }
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+                        }
+                        ++pc;
+                        // ---- feed the T spectra this frame belongs to ----
+                        // frame i contributes h[m] * x to spectrum i - m; slot (i - m) mod TT
+#pragma unroll
+                        for (int m = 0; m < TT; ++m) {
+                            const int js = ((k - m) % TT + TT) % TT;
+#pragma unroll
+                            for (int b = 0; b < NB; ++b) {
+                                if (m == 0) {
+                                    pend[js][b] = make_float2(h[0][b] * v[b].x, h[0][b] * v[b].y);
+                                } else {
+                                    pend[js][b] = fma2(make_float2(h[m][b], h[m][b]), v[b], pend[js][b]);
+                                }
+                            }
+                        }
+                        // ---- spectrum i - TT + 1 is complete ----
+                        const int64_t jspec = i - (TT - 1);
+                        if (ok && jspec >= 0) {
+                            const int jslot = ((k + 1) % TT);
+                            if (brow == 0) {
+                                // new batch: wait until the FFT warps have released this Y buffer
+                                if (bc >= 2 &&
+                                    !__all_sync(0xffffffffu, mbar_wait(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
+                                    *abort_flag = 1;
+                                    ok = false;
+                                }
+                                first_row_spec = jspec;
+                            }
+                            if (!ok) break;
+                            float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW + ypad<G>(q0);
+#pragma unroll
+                            for (int b = 0; b < NB; ++b) yrow[b] = pend[jslot][b];
+                            ++brow;
+                            if (brow == SB || jspec == nspec - 1) {
+                                if (t == 0) {
+                                    meta[bc & 1].out = out_seg + first_row_spec * P;
+                                    meta[bc & 1].nrows = brow;
+                                }
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(yfull0 + 8 * (bc & 1));
+                                ++bc;
+                                brow = 0;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp < C::PRODW) {
+        // ======================= FFT warps =======================
+        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
+        const int ft = threadIdx.x - C::NFT;
+        for (int i = ft; i < C::NTW; i += C::NFFTT) tw[i] = a.tw[i];
+        named_bar_sync<1>(C::NFFTT);
+        uint32_t bc = 0;
+        bool ok = true;
+        int si;
+        int64_t sA, sB;
+        while (ok && ws_next_segment(a, range, si, sA, sB)) {
+            const int64_t nb = (sB - sA + SB - 1) / SB;
+            for (int64_t q = 0; q < nb && ok; ++q, ++bc) {
+                // one thread waits, the decision is broadcast so that every FFT
+                // thread reaches the same named barriers
+                if (ft == 0) meta[2].nrows = mbar_wait(yfull0 + 8 * (bc & 1), (bc >> 1) & 1) ? 1 : 0;
+                named_bar_sync<1>(C::NFFTT);
+                if (!meta[2].nrows) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                const WsMeta mt = meta[bc & 1];
+                float2 *Yb = Y + (bc & 1) * (SB * YROW);
+                ws_passes<P, C::MR, SB, 0, YROW, G>(Yb, W, W + SB * YROW, tw, mt.out, mt.nrows, ft, C::NFFTT,
+                                                    yempty0 + 8 * (bc & 1), C::NFFTT);
+                named_bar_sync<1>(C::NFFTT);  // W buffers free before the next batch
+            }
+        }
+    } else {
+        // ======================= producer warp(group) =======================
+        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
+        if (warp == C::PRODW && lane == 0) {
+            uint32_t pc = 0;
+            bool ok = true;
+            int si;
+            int64_t sA, sB;
+            while (ok && ws_next_segment(a, range, si, sA, sB)) {
+                const StreamDesc &d = a.s[si];
+                const int64_t f_end = sB + TT - 1;
+                for (int64_t f = sA; f < f_end && ok; ++f, ++pc) {
+                    const uint32_t slot = pc % NSLOT;
+                    if (pc >= NSLOT && !mbar_wait(empty0 + 8 * slot, ((pc / NSLOT) + 1) & 1)) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    const uint8_t *src;
+                    if (f < d.n_state) src = static_cast<const uint8_t *>(d.state) + f * (int64_t)C::FB;
+                    else src = static_cast<const uint8_t *>(d.in) + (f - d.n_state) * (int64_t)C::FB;
+                    mbar_expect_tx(full0 + 8 * slot, C::FB);
+                    bulk_g2s(smem_u32(ring + slot * C::FB), src, C::FB, full0 + 8 * slot);
+                }
+            }
+            // drain: every copy issued must have landed before the CTA exits
+            const uint32_t first = pc > NSLOT ? pc - NSLOT : 0;
+            for (uint32_t q = first; q < pc; ++q) {
+                if (!mbar_wait(full0 + 8 * (q % NSLOT), (q / NSLOT) & 1)) *abort_flag = 1;
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
+}
+
+// rows of the launch: one work unit per spectrum
+template <int P, int TT, int IN>
+static pfb_status launch_fft_ws_k(LaunchArgs &a, cudaStream_t stream) {
+    using C = WsCfg<P, TT, IN>;
+    auto k = k_fft_ws<P, TT, IN>;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fft_ws)");
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = sms;
+    }
+    int64_t grid = a.nunits < grid_cap ? a.nunits : grid_cap;
+    if (grid < 1) return PFB_OK;
+    a.units_per_cta = (int32_t)((a.nunits + grid - 1) / grid);
+    grid = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
+    k<<<(unsigned)grid, C::NTHREADS, C::SMEM, stream>>>(a);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_fft_ws");
+    return PFB_OK;
+}
+
+}  // namespace pfb

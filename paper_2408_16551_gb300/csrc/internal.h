@@ -76,6 +76,7 @@ enum KernelFamily : int {
     FAM_FFT_GENERIC = 1,  // fused FIR + radix-2 Stockham FFT, any supported P, T
     FAM_GEMM_F32 = 2,     // fused FIR + DFT-matrix product, FP32 SIMT
     FAM_GEMM_BF16X3 = 3,  // fused FIR + DFT-matrix product, tcgen05 split-bf16
+    FAM_FFT_CLUSTER = 4,  // fused FIR + four-step FFT across a CTA cluster, P in {2048, 4096}
 };
 
 struct Plan {
@@ -117,6 +118,8 @@ pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &args, cudaStream_t stre
 pfb_status launch_fft_generic(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+bool fft_cluster_supported(int P, int T);
 pfb_status prepare_family(const Plan &plan);
 const float *family_taps(const Plan &plan);   // tap layout the family's kernels read
 // work units a stream of S spectra contributes to a launch of the plan's family

@@ -169,13 +169,16 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     p->path = desc->path;
     p->esize = desc->in_dtype == PFB_IN_R32 ? 4 : desc->in_dtype == PFB_IN_C64 ? 8 : 2;
     if (desc->path == PFB_DFT_FFT_F32) {
-        p->family = fft_fast_supported(p->P, p->T) ? FAM_FFT_FAST : FAM_FFT_GENERIC;
+        p->family = fft_fast_supported(p->P, p->T)      ? FAM_FFT_FAST
+                    : fft_cluster_supported(p->P, p->T) ? FAM_FFT_CLUSTER
+                                                        : FAM_FFT_GENERIC;
     } else if (desc->path == PFB_DFT_GEMM_F32) {
         p->family = FAM_GEMM_F32;
     } else {
         p->family = FAM_GEMM_BF16X3;
     }
-    const bool padded = p->family == FAM_FFT_FAST || (p->family == FAM_GEMM_BF16X3 && p->T <= 16);
+    const bool padded = p->family == FAM_FFT_FAST || p->family == FAM_FFT_CLUSTER ||
+                        (p->family == FAM_GEMM_BF16X3 && p->T <= 16);
     p->TT = padded ? fft_fast_tt(p->T) : p->T;
     p->variant = default_variant(*p);
 
@@ -203,6 +206,10 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
         pfb_status st = build_fft_fast_twiddles(*p);
         if (st != PFB_OK) return st;
     }
+    if (p->family == FAM_FFT_CLUSTER) {  // local 1024-point passes of the four-step FFT
+        pfb_status st = build_pass_table(1024, 16, &p->d_tw);
+        if (st != PFB_OK) return st;
+    }
     if (p->family == FAM_GEMM_F32 || p->family == FAM_GEMM_BF16X3) {
         pfb_status st = build_gemm_tables(*p);
         if (st != PFB_OK) return st;
@@ -214,8 +221,8 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
         if (pst != PFB_OK && pst != PFB_ERR_UNSUPPORTED) return pst;
         clear_error();
     }
-    static const char *fam_names[] = {"pfb_fir_fft_f32", "pfb_fir_fft_f32_generic",
-                                      "pfb_fir_dftgemm_f32", "pfb_fir_dftgemm_bf16x3"};
+    static const char *fam_names[] = {"pfb_fir_fft_f32", "pfb_fir_fft_f32_generic", "pfb_fir_dftgemm_f32",
+                                      "pfb_fir_dftgemm_bf16x3", "pfb_fir_fft_f32_cluster"};
     p->kernel_name = fam_names[p->family];
     return PFB_OK;
 }

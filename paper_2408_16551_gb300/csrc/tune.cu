@@ -75,7 +75,13 @@ static void save_file_cache() {
     std::rename((std::string(path) + ".tmp").c_str(), path);
 }
 
-int family_variants(const Plan &plan) { return plan.family == FAM_FFT_FAST ? 5 : 1; }
+int family_variants(const Plan &plan) { return plan.family == FAM_FFT_FAST ? 6 : 1; }
+
+// variant 5 of the fast FFT family needs P >= 128 and T equal to its tap count
+static bool variant_supported(const Plan &plan, int v) {
+    if (plan.family == FAM_FFT_FAST && v == 5) return plan.P >= 128 && plan.T == plan.TT;
+    return v >= 0 && v < family_variants(plan);
+}
 
 int default_variant(const Plan &plan) {
     if (family_variants(plan) <= 1) return 0;
@@ -109,6 +115,7 @@ extern "C" pfb_status pfb_plan_set_variant(pfb_plan_t plan, int32_t variant) {
     if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
     Plan &p = *reinterpret_cast<Plan *>(plan);
     if (variant < 0 || variant >= family_variants(p)) return fail(PFB_ERR_INVALID, "variant out of range");
+    if (!variant_supported(p, variant)) return fail(PFB_ERR_UNSUPPORTED, "variant not available for this P/T");
     p.variant = variant;
     return prepare_family(p);
 }
@@ -138,6 +145,7 @@ extern "C" pfb_status pfb_plan_autotune(pfb_plan_t plan, int64_t n_samples, void
     float best_ms = 1e30f;
     const int saved = p.variant;
     for (int v = 0; st == PFB_OK && v < nv; ++v) {
+        if (!variant_supported(p, v)) continue;
         p.variant = v;
         st = prepare_family(p);
         if (st != PFB_OK) break;

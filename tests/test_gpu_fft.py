@@ -37,11 +37,12 @@ FAST = [(P, T, dt) for P in (64, 128, 256, 512, 1024)
         for (T, dt) in ((16, synth.IN_C64), (8, synth.IN_R32), (4, synth.IN_CI8), (3, synth.IN_C64),
                         (1, synth.IN_C64), (12, synth.IN_CI8))]
 GENERIC = [(4, 2, synth.IN_C64), (8, 3, synth.IN_R32), (16, 4, synth.IN_R32), (32, 16, synth.IN_CI8),
-           (64, 17, synth.IN_C64), (1024, 64, synth.IN_C64), (2048, 16, synth.IN_C64), (4096, 16, synth.IN_CI8),
-           (4096, 8, synth.IN_C64)]
+           (64, 17, synth.IN_C64), (1024, 64, synth.IN_C64), (4096, 20, synth.IN_C64), (2048, 33, synth.IN_CI8)]
+CLUSTER = [(2048, 16, synth.IN_C64), (4096, 16, synth.IN_CI8), (4096, 8, synth.IN_C64), (4096, 16, synth.IN_C64),
+           (2048, 4, synth.IN_R32), (4096, 3, synth.IN_C64), (4096, 12, synth.IN_R32)]
 
 
-@pytest.mark.parametrize("P,T,dt", FAST + GENERIC)
+@pytest.mark.parametrize("P,T,dt", FAST + GENERIC + CLUSTER)
 def test_fft_path_parity(P, T, dt):
     n = P * (T - 1 + 8 * 5 + 3) + 7          # 5 full units + 3 spectra + a partial frame
     plan, x, got = _run(P, T, dt, n, seed=P + T)
@@ -53,7 +54,10 @@ def test_fft_path_parity(P, T, dt):
 def test_fast_family_is_selected():
     for P, T in ((64, 16), (1024, 16), (256, 8)):
         assert pkg.Plan(P, T).kernel_name == "pfb_fir_fft_f32"
-    assert pkg.Plan(4096, 16).kernel_name == "pfb_fir_fft_f32_generic"
+    assert pkg.Plan(4096, 16).kernel_name == "pfb_fir_fft_f32_cluster"
+    assert pkg.Plan(2048, 8).kernel_name == "pfb_fir_fft_f32_cluster"
+    assert pkg.Plan(4096, 20).kernel_name == "pfb_fir_fft_f32_generic"
+    assert pkg.Plan(32, 16).kernel_name == "pfb_fir_fft_f32_generic"
 
 
 @pytest.mark.parametrize("P,T", [(64, 4), (1024, 16), (4096, 16), (16, 4)])
@@ -200,18 +204,23 @@ def test_execute_host_matches_device():
 
 
 @pytest.mark.parametrize("P,T,dt", [(1024, 16, synth.IN_C64), (512, 8, synth.IN_CI8), (256, 16, synth.IN_R32),
-                                    (128, 4, synth.IN_C64), (64, 12, synth.IN_C64)])
+                                    (128, 4, synth.IN_C64), (64, 12, synth.IN_C64), (1024, 8, synth.IN_CI8),
+                                    (1024, 4, synth.IN_R32), (512, 16, synth.IN_C64), (1024, 12, synth.IN_C64)])
 def test_every_fast_variant_matches_oracle(P, T, dt):
     import torch
     n = P * (T - 1 + 8 * 7 + 5) + 3
     x = synth.small_stream(P, T, n, in_dtype=dt, seed=77).generate()
     ref = reference(x, dt, P, T, synth.WIN_HAMMING)
     plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_HAMMING)
-    assert plan.num_variants == 5
+    assert plan.num_variants == 6
     xd = to_device(x)
     outs = []
     for v in range(plan.num_variants):
-        plan.variant = v
+        try:
+            plan.variant = v
+        except pkg.PFBError as e:      # variant 5 needs P >= 128 and T in {4, 8, 16}
+            assert e.status == pkg.PFB_ERR_UNSUPPORTED and v == 5 and (P < 128 or T not in (4, 8, 16))
+            continue
         assert plan.variant == v
         got = plan.execute(xd).cpu().numpy()
         assert_close(got, ref, what=f"variant {v} P={P} T={T}")
@@ -229,3 +238,33 @@ def test_autotune_picks_a_variant_and_keeps_results():
     assert_close(got, reference(x, synth.IN_C64, P, T, synth.WIN_HANN))
     with pytest.raises(pkg.PFBError):
         plan.variant = 9
+
+
+@pytest.mark.parametrize("P,T", [(1024, 16), (256, 8)])
+def test_ws_variant_streams_and_batches(P, T):
+    """Warp-specialised variant: several streams in one launch (segments that
+    start mid-range), chunked serving with resident state, bitwise equality."""
+    import torch
+    shapes = [P * 300 + 17, P * (T + 1), P * 40, P * (T - 1)]     # the last one gives 0 spectra
+    plans, xs, singles = [], [], []
+    for i, n in enumerate(shapes):
+        plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_BLACKMAN)
+        plan.variant = 5
+        x = synth.small_stream(P, T, n, seed=60 + i).generate()
+        xd = to_device(x)
+        plans.append(plan); xs.append((x, xd))
+        if plan.out_spectra(n) > 0:
+            got = plan.execute(xd)
+            assert_close(got.cpu().numpy(), reference(x, synth.IN_C64, P, T, synth.WIN_BLACKMAN), what=f"ws {i}")
+            singles.append(got.clone())
+        else:
+            singles.append(None)
+    entries = []
+    for plan, (x, xd), n in zip(plans, xs, shapes):
+        S = plan.out_spectra(n)
+        entries.append((plan, xd, torch.zeros((max(S, 1), P), dtype=torch.complex64, device="cuda")))
+    pkg.pfb_execute_batch(entries)
+    torch.cuda.synchronize()
+    for (plan, xd, out), ref in zip(entries, singles):
+        if ref is not None:
+            assert torch.equal(out[:ref.shape[0]], ref)
