@@ -236,8 +236,8 @@ def run_serving(pkg, n_requests, rate_hz, warm_requests, device):
     bufs = [torch.from_numpy(rng.integers(-127, 128, size=2 * wl.request_samples, dtype=np.int16).astype(np.int8)).to(device)
             for _ in range(nbuf)]
     nch = wl.request_samples // wl.chunk_samples
-    out_rows = wl.chunk_samples // wl.P  # spectra a chunk emits once the state is full
-    outs = [torch.empty((nch, out_rows, wl.P), dtype=torch.complex64, device=device) for _ in range(nbuf)]
+    s_req = plan.out_spectra(wl.request_samples)      # spectra of a whole request (state starts empty)
+    outs = [torch.empty((s_req, wl.P), dtype=torch.complex64, device=device) for _ in range(nbuf)]
     arrivals = wl.arrivals()
     torch.cuda.synchronize()
     pending = []  # (req index, sid, last ticket, t_arrival)
@@ -252,9 +252,11 @@ def run_serving(pkg, n_requests, rate_hz, warm_requests, device):
             b = i % nbuf
             sid = srv.open_stream(plan)
             last = None
+            row = 0
             for c in range(nch):
                 S = srv.next_spectra(sid, wl.chunk_samples)
-                o = outs[b][c]
+                o = outs[b][row:row + S]
+                row += S
                 last = srv.submit(sid, bufs[b][2 * c * wl.chunk_samples: 2 * (c + 1) * wl.chunk_samples],
                                   wl.chunk_samples, o if S > 0 else None)
             pending.append((i, sid, last, t_start + arrivals[i]))
@@ -286,6 +288,7 @@ def run_serving(pkg, n_requests, rate_hz, warm_requests, device):
                         f"in {nch} chunks of {wl.chunk_samples}, filter state resident on the device",
             "p50_us": lat[len(lat) // 2], "p99_us": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))],
             "gsps": done_samples / span / 1e9, "chunk_p50_us": stats["p50_latency_us"],
+            "mean_batch": stats["batched_requests"] / max(stats["batches"], 1),
             "chunk_p99_us": stats["p99_latency_us"], "failed": stats["failed"],
             "peak_reserved_bytes": stats["peak_reserved_bytes"]}
 

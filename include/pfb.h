@@ -199,6 +199,7 @@ typedef struct pfb_server_stats {
     int64_t queued_now, in_flight_now;
     int64_t reserved_bytes_now, peak_reserved_bytes;
     int64_t samples_completed;
+    int64_t batches, batched_requests;  /* launches formed so far and requests they held */
     double p50_latency_us, p99_latency_us, mean_latency_us; /* submit -> completion */
 } pfb_server_stats;
 

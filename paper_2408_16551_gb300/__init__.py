@@ -60,7 +60,7 @@ class pfb_server_desc(ctypes.Structure):
 class pfb_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "rejected", "queued_now",
                                               "in_flight_now", "reserved_bytes_now", "peak_reserved_bytes",
-                                              "samples_completed")] + \
+                                              "samples_completed", "batches", "batched_requests")] + \
                [(n, ctypes.c_double) for n in ("p50_latency_us", "p99_latency_us", "mean_latency_us")]
 
 

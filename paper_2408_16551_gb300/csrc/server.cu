@@ -1,28 +1,35 @@
 // Serving: continuous batching of channelisation requests.
 //
 // A request is one chunk of one stream.  Each stream keeps its filter state on
-// the device -- the last T-1 frames of raw input -- so that chunk c sees
+// the device -- the last T-1 frames of raw input -- so that a chunk sees
 // state ++ chunk as its frame sequence and the concatenated outputs equal the
 // single-pass channeliser on the concatenated input (spectra are the "valid"
 // outputs of Sec. 5.2's per-branch FIR).  State lives in two device buffers
-// per stream (read one, write the other), so consecutive chunks of a stream
-// can be queued back to back on the stream's CUDA stream without host waits.
+// per stream (read one, write the other).
 //
-// Admission: requests are taken in submission order; one is launched when
-// fewer than max_slots requests are on the device and the bytes it pins (its
-// input and output buffers) fit in the HBM budget next to the resident state
-// of all open streams.  Requests of different streams run on different CUDA
-// streams of a pool and overlap on the device.  A host scheduler thread
-// admits queued requests and observes completions (cudaEventQuery every few
-// microseconds while work is in flight); latency is submit -> observed
-// completion.  A request whose completion is not seen within timeout_ms
-// reports PFB_ERR_TIMEOUT; its slot stays held until the device finishes it.
+// Scheduling (host worker thread): at every step it polls the batches on the
+// device and forms the next batch from the queue, in submission order, while
+// fewer than max_slots requests are on the device and the bytes they pin
+// (input and output buffers) fit the HBM budget next to the resident state of
+// the open streams.  A batch is one kernel launch per kernel variant over all
+// its streams (the persistent launch of pfb_execute_batch), one batched state
+// update and one event.  Consecutive chunks of a stream whose input and output
+// buffers continue each other merge into one descriptor; any other chunk of a
+// stream already in the batch waits for a later batch.  Batches rotate over a
+// small pool of CUDA streams and wait (cudaStreamWaitEvent) on the previous
+// batch of each of their streams, so independent work overlaps on the device
+// while each stream's chunks run in order.  Requests that arrive while others
+// run join the next batch.  Latency is submit -> observed completion (the
+// batch event, polled every few microseconds).  A request not seen complete
+// within timeout_ms reports PFB_ERR_TIMEOUT; its slot stays held until the
+// device finishes it.
 //
 // Host-side fault injection for tests (no GPU fault is ever provoked):
-//   PFB_FAULT=launch_fail:<k>   the k-th launch attempt (1-based) is not issued
-//                               and its request fails with PFB_ERR_CUDA;
+//   PFB_FAULT=launch_fail:<k>      the k-th request taken into a batch is not
+//                                  launched and fails with PFB_ERR_CUDA (later
+//                                  chunks of its stream fail too);
 //   PFB_FAULT=lose_completion:<k>  the k-th launched request's completion is
-//                               never observed, so it times out.
+//                                  never observed, so it times out.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -40,34 +47,61 @@ namespace pfb {
 
 using Clock = std::chrono::steady_clock;
 
-// new_state[i] = frame (old_frames + chunk_frames - n_keep + i) of (state ++ chunk)
-__global__ void k_state_update(const uint2 *old_state, int64_t old_frames, const uint2 *chunk, int64_t chunk_frames,
-                               uint2 *new_state, int64_t n_keep, int64_t words_per_frame) {
-    const int64_t total = n_keep * words_per_frame;
-    const int64_t first = old_frames + chunk_frames - n_keep;
+// new_state[i] = frame (old_frames + chunk_frames - n_keep + i) of (state ++ chunk),
+// for up to kMaxStateUpdates streams per launch (one block row per stream)
+struct StateUpdate {
+    const uint2 *old_state;
+    const uint2 *chunk;
+    uint2 *new_state;
+    int64_t old_frames, chunk_frames, n_keep, words_per_frame;
+};
+constexpr int kMaxStateUpdates = 64;
+struct StateUpdateArgs {
+    StateUpdate u[kMaxStateUpdates];
+    int n;
+};
+
+__global__ void k_state_update(const __grid_constant__ StateUpdateArgs a) {
+    const StateUpdate &u = a.u[blockIdx.y];
+    const int64_t total = u.n_keep * u.words_per_frame;
+    const int64_t first = u.old_frames + u.chunk_frames - u.n_keep;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = w / words_per_frame, off = w - i * words_per_frame;
+        const int64_t i = w / u.words_per_frame, off = w - i * u.words_per_frame;
         const int64_t g = first + i;
-        new_state[w] = (g < old_frames) ? old_state[g * words_per_frame + off]
-                                        : chunk[(g - old_frames) * words_per_frame + off];
+        u.new_state[w] = (g < u.old_frames) ? u.old_state[g * u.words_per_frame + off]
+                                            : u.chunk[(g - u.old_frames) * u.words_per_frame + off];
     }
+}
+
+static pfb_status launch_state_updates(const std::vector<StateUpdate> &ups, cudaStream_t stream) {
+    for (size_t g0 = 0; g0 < ups.size(); g0 += kMaxStateUpdates) {
+        StateUpdateArgs a;
+        std::memset(&a, 0, sizeof(a));
+        int64_t maxw = 0;
+        for (size_t i = g0; i < ups.size() && a.n < kMaxStateUpdates; ++i) {
+            if (ups[i].n_keep <= 0) continue;
+            a.u[a.n++] = ups[i];
+            maxw = std::max(maxw, ups[i].n_keep * ups[i].words_per_frame);
+        }
+        if (a.n == 0) continue;
+        const int threads = 256;
+        const unsigned bx = (unsigned)std::min<int64_t>((maxw + threads - 1) / threads, 64);
+        k_state_update<<<dim3(bx, a.n), threads, 0, stream>>>(a);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "launch k_state_update");
+    }
+    return PFB_OK;
 }
 
 pfb_status launch_state_update(const void *old_state, int64_t old_frames, const void *chunk, int64_t chunk_frames,
                                void *new_state, int64_t n_keep, int64_t frame_bytes, cudaStream_t stream) {
-    if (n_keep <= 0) return PFB_OK;
-    const int64_t wpf = frame_bytes / 8;
-    const int64_t total = n_keep * wpf;
-    const int threads = 256;
-    const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 1024);
-    k_state_update<<<blocks, threads, 0, stream>>>(static_cast<const uint2 *>(old_state), old_frames,
-                                                   static_cast<const uint2 *>(chunk), chunk_frames,
-                                                   static_cast<uint2 *>(new_state), n_keep, wpf);
-    g_launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_state_update");
-    return PFB_OK;
+    StateUpdate u{static_cast<const uint2 *>(old_state), static_cast<const uint2 *>(chunk),
+                  static_cast<uint2 *>(new_state), old_frames, chunk_frames, n_keep, frame_bytes / 8};
+    return launch_state_updates({u}, stream);
 }
+
+struct Batch;
 
 struct Request {
     int64_t ticket = 0, stream_id = 0;
@@ -75,9 +109,8 @@ struct Request {
     void *d_out = nullptr;
     int64_t n_samples = 0, S = 0, bytes = 0;
     pfb_status status = PFB_PENDING;
-    bool launched = false, lost = false;
-    int pool_index = 0;
-    cudaEvent_t done = nullptr;
+    bool launched = false, lost = false, released = false;
+    Batch *batch = nullptr;
     Clock::time_point t_submit, t_launch, t_done;
 };
 
@@ -90,8 +123,20 @@ struct PStream {
     int64_t frames_submitted = 0;   // frames of all chunks submitted so far
     int64_t state_bytes = 0;
     int64_t outstanding = 0;        // submitted and not finished
-    int pool_index = 0;
+    bool failed = false;            // an earlier chunk failed: later chunks fail too
     bool closing = false;
+    cudaEvent_t last_event = nullptr;  // event of the last batch that advanced this stream
+    int last_cs = -1;                  // CUDA stream that batch ran on
+};
+
+// A batch: every request admitted at one scheduling step, run as one launch
+// per kernel variant plus one batched state update, completing on one event.
+struct Batch {
+    std::vector<Request *> reqs;
+    cudaEvent_t done = nullptr;
+    int cs = 0;
+    Clock::time_point t_launch;
+    bool device_done = false;
 };
 
 struct Server {
@@ -102,13 +147,17 @@ struct Server {
     std::thread worker;
     bool stop = false;
     std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> free_events;
     std::map<int64_t, std::unique_ptr<PStream>> streams;
     std::map<int64_t, std::unique_ptr<Request>> tickets;
-    std::deque<Request *> queue;      // submitted, not launched (submission order)
-    std::vector<Request *> inflight;  // launched, completion not observed
+    std::deque<Request *> queue;             // submitted, not launched (submission order)
+    std::vector<std::unique_ptr<Batch>> batches;  // launched, device completion not seen
+    int64_t inflight = 0;                    // requests launched and still holding a slot
+    int next_cs = 0;
     int64_t next_stream = 1, next_ticket = 1;
     int64_t reserved = 0, peak_reserved = 0;
     int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_rejected = 0, samples_completed = 0;
+    int64_t n_batches = 0, n_batched_requests = 0;
     std::vector<double> latencies_us;
     int64_t launch_attempts = 0, launches_done = 0;
     int64_t fault_launch_fail = -1, fault_lose = -1;
@@ -127,46 +176,6 @@ static void parse_faults(Server &s) {
     s.fault_lose = num("lose_completion");
 }
 
-// Launch one request (mutex held).  Returns the request's status.
-static pfb_status launch_request(Server &s, Request &r) {
-    PStream &ps = *s.streams.at(r.stream_id);
-    Plan &plan = *ps.plan;
-    cudaStream_t cs = s.pool[ps.pool_index];
-    r.pool_index = ps.pool_index;
-    r.t_launch = Clock::now();
-    s.launch_attempts++;
-    if (s.launch_attempts == s.fault_launch_fail) return fail(PFB_ERR_CUDA, "injected launch failure");
-    const int64_t F = r.n_samples / plan.P;
-    const int64_t n_frames = ps.state_frames + F;
-    if (r.S > 0) {
-        StreamDesc d;
-        std::memset(&d, 0, sizeof(d));
-        d.in = r.d_chunk;
-        d.state = ps.state[ps.cur];
-        d.out = static_cast<float2 *>(r.d_out);
-        d.n_state = ps.state_frames;
-        d.n_frames = n_frames;
-        d.S = r.S;
-        d.taps = family_taps(plan);
-        d.scale = plan.desc.in_scale;
-        d.T = plan.T;
-        pfb_status st = launch_family(plan, &d, 1, cs);
-        if (st != PFB_OK) return st;
-    }
-    const int64_t keep = std::min<int64_t>(plan.T - 1, n_frames);
-    pfb_status st = launch_state_update(ps.state[ps.cur], ps.state_frames, r.d_chunk, F, ps.state[ps.cur ^ 1], keep,
-                                        (int64_t)plan.P * plan.esize, cs);
-    if (st != PFB_OK) return st;
-    ps.cur ^= 1;
-    ps.state_frames = keep;
-    cudaError_t e = cudaEventRecord(r.done, cs);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    r.launched = true;
-    s.launches_done++;
-    if (s.launches_done == s.fault_lose) r.lost = true;
-    return PFB_OK;
-}
-
 static void finish(Server &s, Request &r, pfb_status st) {
     r.status = st;
     r.t_done = Clock::now();
@@ -178,50 +187,204 @@ static void finish(Server &s, Request &r, pfb_status st) {
         s.latencies_us.push_back(std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count());
     } else {
         s.n_failed++;
+        if (st != PFB_ERR_TIMEOUT) ps.failed = true;
     }
 }
 
-// Admit queued requests in submission order while slots and budget allow.
-static void admit(Server &s) {
-    while (!s.queue.empty()) {
-        Request *r = s.queue.front();
-        if ((int64_t)s.inflight.size() >= s.desc.max_slots) return;
-        if (s.reserved + r->bytes > s.desc.hbm_budget_bytes) return;
-        s.queue.pop_front();
-        pfb_status st = launch_request(s, *r);
-        if (st == PFB_OK) {
-            s.reserved += r->bytes;
-            s.peak_reserved = std::max(s.peak_reserved, s.reserved);
-            s.inflight.push_back(r);
+static cudaEvent_t get_event(Server &s) {
+    if (!s.free_events.empty()) {
+        cudaEvent_t e = s.free_events.back();
+        s.free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Form and launch one batch from the queue (mutex held).  Requests are taken
+// in submission order while slots and budget allow; a stream contributes one
+// run of chunks whose input and output buffers continue each other (merged
+// into one descriptor); a chunk that does not continue the run waits for a
+// later batch, so each stream's chunks run in submission order.
+static void launch_batch(Server &s) {
+    if (s.queue.empty()) return;
+    std::vector<Request *> picked;
+    std::map<int64_t, Request *> tail;   // last picked request of each stream
+    std::map<int64_t, bool> blocked;
+    int64_t bytes = 0;
+    for (size_t i = 0; i < s.queue.size(); ++i) {
+        Request *r = s.queue[i];
+        if (blocked[r->stream_id]) continue;
+        if (s.inflight + (int64_t)picked.size() >= s.desc.max_slots) break;
+        if (s.reserved + bytes + r->bytes > s.desc.hbm_budget_bytes) break;
+        auto t = tail.find(r->stream_id);
+        if (t != tail.end()) {
+            const Request *p = t->second;
+            const PStream &ps = *s.streams.at(r->stream_id);
+            const char *in_end = static_cast<const char *>(p->d_chunk) + p->n_samples * ps.plan->esize;
+            const float2 *out_end = static_cast<const float2 *>(p->d_out) + p->S * ps.plan->P;
+            const bool cont = in_end == static_cast<const char *>(r->d_chunk) &&
+                              (r->S == 0 || p->S == 0 || out_end == static_cast<const float2 *>(r->d_out));
+            if (!cont) {
+                blocked[r->stream_id] = true;
+                continue;
+            }
+        }
+        picked.push_back(r);
+        tail[r->stream_id] = r;
+        bytes += r->bytes;
+    }
+    if (picked.empty()) return;
+    for (Request *r : picked) {
+        auto it = std::find(s.queue.begin(), s.queue.end(), r);
+        s.queue.erase(it);
+    }
+    // injected launch failures, and streams that already failed
+    std::vector<Request *> go;
+    for (Request *r : picked) {
+        s.launch_attempts++;
+        PStream &ps = *s.streams.at(r->stream_id);
+        if (s.launch_attempts == s.fault_launch_fail) {
+            finish(s, *r, fail(PFB_ERR_CUDA, "injected launch failure"));
+        } else if (ps.failed) {
+            finish(s, *r, fail(PFB_ERR_CUDA, "an earlier chunk of this stream failed"));
         } else {
-            finish(s, *r, st);
+            go.push_back(r);
         }
     }
+    if (go.empty()) return;
+    auto b = std::make_unique<Batch>();
+    b->cs = s.next_cs++ % (int)s.pool.size();
+    cudaStream_t cs = s.pool[b->cs];
+    b->t_launch = Clock::now();
+    // order after the previous batch of every stream in this one
+    std::vector<cudaEvent_t> waited;
+    for (Request *r : go) {
+        PStream &ps = *s.streams.at(r->stream_id);
+        if (ps.last_event && ps.last_cs != b->cs &&
+            std::find(waited.begin(), waited.end(), ps.last_event) == waited.end()) {
+            cudaStreamWaitEvent(cs, ps.last_event, 0);
+            waited.push_back(ps.last_event);
+        }
+    }
+    // one descriptor per stream run, one launch per plan
+    std::map<Plan *, std::vector<StreamDesc>> groups;
+    std::vector<StateUpdate> ups;
+    std::map<int64_t, std::vector<Request *>> runs;
+    std::vector<int64_t> order;
+    for (Request *r : go) {
+        if (runs.find(r->stream_id) == runs.end()) order.push_back(r->stream_id);
+        runs[r->stream_id].push_back(r);
+    }
+    pfb_status st = PFB_OK;
+    for (int64_t sid : order) {
+        PStream &ps = *s.streams.at(sid);
+        Plan &plan = *ps.plan;
+        const auto &rr = runs[sid];
+        int64_t F = 0, S = 0;
+        for (Request *r : rr) {
+            F += r->n_samples / plan.P;
+            S += r->S;
+        }
+        const int64_t n_frames = ps.state_frames + F;
+        if (S > 0) {
+            StreamDesc d;
+            std::memset(&d, 0, sizeof(d));
+            d.in = rr.front()->d_chunk;
+            d.state = ps.state[ps.cur];
+            // the run's output starts at its first chunk that emits spectra
+            for (Request *r : rr)
+                if (r->S > 0) {
+                    d.out = static_cast<float2 *>(r->d_out);
+                    break;
+                }
+            d.n_state = ps.state_frames;
+            d.n_frames = n_frames;
+            d.S = S;
+            d.taps = family_taps(plan);
+            d.scale = plan.desc.in_scale;
+            d.T = plan.T;
+            groups[&plan].push_back(d);
+        }
+        const int64_t keep = std::min<int64_t>(plan.T - 1, n_frames);
+        ups.push_back(StateUpdate{static_cast<const uint2 *>(ps.state[ps.cur]), static_cast<const uint2 *>(rr.front()->d_chunk),
+                                  static_cast<uint2 *>(ps.state[ps.cur ^ 1]), ps.state_frames, F, keep,
+                                  (int64_t)plan.P * plan.esize / 8});
+        ps.cur ^= 1;
+        ps.state_frames = keep;
+    }
+    for (auto &g : groups) {
+        if (st == PFB_OK) st = launch_family(*g.first, g.second.data(), (int)g.second.size(), cs);
+    }
+    if (st == PFB_OK) st = launch_state_updates(ups, cs);
+    b->done = get_event(s);
+    if (st == PFB_OK && (!b->done || cudaEventRecord(b->done, cs) != cudaSuccess)) st = fail(PFB_ERR_CUDA, "event record");
+    if (st != PFB_OK) {
+        for (Request *r : go) finish(s, *r, st);
+        if (b->done) s.free_events.push_back(b->done);
+        return;
+    }
+    for (int64_t sid : order) {
+        PStream &ps = *s.streams.at(sid);
+        ps.last_event = b->done;
+        ps.last_cs = b->cs;
+    }
+    for (Request *r : go) {
+        r->launched = true;
+        r->batch = b.get();
+        r->t_launch = b->t_launch;
+        s.launches_done++;
+        if (s.launches_done == s.fault_lose) r->lost = true;
+        s.reserved += r->bytes;
+        s.inflight++;
+        b->reqs.push_back(r);
+    }
+    s.peak_reserved = std::max(s.peak_reserved, s.reserved);
+    s.n_batches++;
+    s.n_batched_requests += (int64_t)go.size();
+    s.batches.push_back(std::move(b));
 }
 
 static void poll_inflight(Server &s) {
     const auto now = Clock::now();
-    for (size_t i = 0; i < s.inflight.size();) {
-        Request *r = s.inflight[i];
-        cudaError_t q = r->lost ? cudaErrorNotReady : cudaEventQuery(r->done);
-        bool device_done = (q == cudaSuccess);
-        if (q != cudaSuccess && q != cudaErrorNotReady) {
-            cudaGetLastError();
-            device_done = true;
-        }
-        if (r->status == PFB_PENDING) {
-            if (device_done) {
-                finish(s, *r, q == cudaSuccess ? PFB_OK : PFB_ERR_CUDA);
-            } else if (std::chrono::duration<double, std::milli>(now - r->t_launch).count() > s.desc.timeout_ms) {
-                finish(s, *r, PFB_ERR_TIMEOUT);
+    for (size_t i = 0; i < s.batches.size();) {
+        Batch &b = *s.batches[i];
+        if (!b.device_done) {
+            cudaError_t q = cudaEventQuery(b.done);
+            if (q == cudaSuccess) {
+                b.device_done = true;
+            } else if (q != cudaErrorNotReady) {
+                cudaGetLastError();
+                b.device_done = true;
+                for (Request *r : b.reqs)
+                    if (r->status == PFB_PENDING && !r->lost) finish(s, *r, PFB_ERR_CUDA);
             }
         }
-        // the slot and the budget are released only once the device is done
-        // (a timed-out request whose completion is lost keeps holding them)
-        if (device_done && !r->lost) {
-            s.reserved -= r->bytes;
-            s.inflight[i] = s.inflight.back();
-            s.inflight.pop_back();
+        bool all_released = true;
+        for (Request *r : b.reqs) {
+            if (r->status == PFB_PENDING) {
+                if (b.device_done && !r->lost) {
+                    finish(s, *r, PFB_OK);
+                } else if (std::chrono::duration<double, std::milli>(now - r->t_launch).count() > s.desc.timeout_ms) {
+                    finish(s, *r, PFB_ERR_TIMEOUT);
+                }
+            }
+            // slots and budget are released once the device is done with the
+            // request (a request whose completion was lost keeps holding them)
+            if (!r->released && b.device_done && !r->lost) {
+                r->released = true;
+                s.reserved -= r->bytes;
+                s.inflight--;
+            }
+            if (!r->released) all_released = false;
+        }
+        if (b.device_done && all_released) {
+            for (auto &kv : s.streams)
+                if (kv.second->last_event == b.done) kv.second->last_event = nullptr;
+            s.free_events.push_back(b.done);
+            s.batches[i] = std::move(s.batches.back());
+            s.batches.pop_back();
         } else {
             ++i;
         }
@@ -233,16 +396,16 @@ static void worker_loop(Server *sp) {
     cudaSetDevice(s.device);
     std::unique_lock<std::mutex> lk(s.mu);
     while (!s.stop) {
-        if (s.inflight.empty() && s.queue.empty()) {
-            s.cv_work.wait(lk, [&] { return s.stop || !s.inflight.empty() || !s.queue.empty(); });
+        if (s.batches.empty() && s.queue.empty()) {
+            s.cv_work.wait(lk, [&] { return s.stop || !s.batches.empty() || !s.queue.empty(); });
             continue;
         }
-        size_t before = s.n_completed + s.n_failed;
+        const int64_t before = s.n_completed + s.n_failed;
         poll_inflight(s);
-        admit(s);
-        if ((size_t)(s.n_completed + s.n_failed) != before) s.cv_done.notify_all();
+        launch_batch(s);
+        if (s.n_completed + s.n_failed != before) s.cv_done.notify_all();
         lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(5));
+        std::this_thread::sleep_for(std::chrono::microseconds(2));
         lk.lock();
     }
 }
@@ -300,12 +463,12 @@ extern "C" pfb_status pfb_server_destroy(pfb_server_t server) {
         // bounded wait for queued and in-flight work
         std::unique_lock<std::mutex> lk(s->mu);
         const auto limit = Clock::now() + std::chrono::milliseconds((int64_t)s->desc.timeout_ms * 2 + 100);
-        while ((!s->inflight.empty() || !s->queue.empty()) && Clock::now() < limit) {
+        while ((!s->batches.empty() || !s->queue.empty()) && Clock::now() < limit) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(200));
             lk.lock();
         }
-        if (!s->inflight.empty() || !s->queue.empty()) result = fail(PFB_ERR_TIMEOUT, "work still in flight at destroy");
+        if (!s->batches.empty() || !s->queue.empty()) result = fail(PFB_ERR_TIMEOUT, "work still in flight at destroy");
         s->stop = true;
     }
     s->cv_work.notify_all();
@@ -314,8 +477,9 @@ extern "C" pfb_status pfb_server_destroy(pfb_server_t server) {
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
     for (auto cs : s->pool) cudaStreamSynchronize(cs);
-    for (auto &kv : s->tickets)
-        if (kv.second->done) cudaEventDestroy(kv.second->done);
+    for (auto &b : s->batches)
+        if (b->done) cudaEventDestroy(b->done);
+    for (auto e : s->free_events) cudaEventDestroy(e);
     for (auto &kv : s->streams) {
         cudaFree(kv.second->state[0]);
         cudaFree(kv.second->state[1]);
@@ -350,7 +514,6 @@ extern "C" pfb_status pfb_stream_open(pfb_server_t server, pfb_plan_t plan, int6
     ps->id = s.next_stream++;
     ps->plan = p;
     ps->state_bytes = 2 * bytes;
-    ps->pool_index = (int)(ps->id % (int64_t)s.pool.size());
     s.reserved += ps->state_bytes;
     s.peak_reserved = std::max(s.peak_reserved, s.reserved);
     *out_stream_id = ps->id;
@@ -378,8 +541,9 @@ extern "C" pfb_status pfb_stream_close(pfb_server_t server, int64_t stream_id) {
     bool busy = true;
     while (busy && Clock::now() < limit) {
         busy = false;
-        for (Request *r : s.inflight)
-            if (r->stream_id == stream_id) busy = true;
+        for (auto &b : s.batches)
+            for (Request *r : b->reqs)
+                if (r->stream_id == stream_id && !r->released) busy = true;
         if (busy) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(100));
@@ -390,7 +554,7 @@ extern "C" pfb_status pfb_stream_close(pfb_server_t server, int64_t stream_id) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(s.device);
-    cudaStreamSynchronize(s.pool[ps.pool_index]);
+    if (ps.last_event) cudaEventSynchronize(ps.last_event);
     cudaFree(ps.state[0]);
     cudaFree(ps.state[1]);
     cudaSetDevice(prev);
@@ -435,7 +599,7 @@ extern "C" pfb_status pfb_submit(pfb_server_t server, int64_t stream_id, const v
     if (out_cap_spectra < S) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
     const int64_t bytes = n_samples * plan.esize + S * plan.P * (int64_t)sizeof(float2);
     if (bytes + ps.state_bytes > s.desc.hbm_budget_bytes) return fail(PFB_ERR_BUSY, "request larger than the budget");
-    const bool fits = s.queue.empty() && (int64_t)s.inflight.size() < s.desc.max_slots &&
+    const bool fits = s.queue.empty() && s.inflight < s.desc.max_slots &&
                       s.reserved + bytes <= s.desc.hbm_budget_bytes;
     if (!fits && !s.desc.queue_when_busy) {
         s.n_rejected++;
@@ -450,14 +614,6 @@ extern "C" pfb_status pfb_submit(pfb_server_t server, int64_t stream_id, const v
     r->S = S;
     r->bytes = bytes;
     r->t_submit = t0;
-    int prev = 0;
-    cudaGetDevice(&prev);
-    if (prev != s.device) cudaSetDevice(s.device);
-    cudaError_t e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        if (prev != s.device) cudaSetDevice(prev);
-        return cuda_fail(e, "cudaEventCreate");
-    }
     ps.frames_submitted += n_samples / plan.P;
     ps.outstanding++;
     s.n_submitted++;
@@ -465,8 +621,6 @@ extern "C" pfb_status pfb_submit(pfb_server_t server, int64_t stream_id, const v
     *out_ticket = r->ticket;
     s.tickets[r->ticket] = std::move(r);
     s.queue.push_back(rp);
-    admit(s);  // launch right away when a slot and budget are free
-    if (prev != s.device) cudaSetDevice(prev);
     lk.unlock();
     s.cv_work.notify_all();
     return PFB_OK;
@@ -506,10 +660,12 @@ extern "C" pfb_status pfb_server_get_stats(pfb_server_t server, pfb_server_stats
     out->failed = s.n_failed;
     out->rejected = s.n_rejected;
     out->queued_now = (int64_t)s.queue.size();
-    out->in_flight_now = (int64_t)s.inflight.size();
+    out->in_flight_now = s.inflight;
     out->reserved_bytes_now = s.reserved;
     out->peak_reserved_bytes = s.peak_reserved;
     out->samples_completed = s.samples_completed;
+    out->batches = s.n_batches;
+    out->batched_requests = s.n_batched_requests;
     if (!s.latencies_us.empty()) {
         std::vector<double> v = s.latencies_us;
         std::sort(v.begin(), v.end());

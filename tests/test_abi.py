@@ -93,4 +93,4 @@ def test_struct_layouts():
     assert ctypes.sizeof(pkg.pfb_plan_desc) == 40
     assert ctypes.sizeof(pkg.pfb_batch_item) == 40
     assert ctypes.sizeof(pkg.pfb_server_desc) == 24
-    assert ctypes.sizeof(pkg.pfb_server_stats) == 9 * 8 + 3 * 8
+    assert ctypes.sizeof(pkg.pfb_server_stats) == 11 * 8 + 3 * 8
