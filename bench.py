@@ -293,6 +293,85 @@ def run_serving(pkg, n_requests, rate_hz, warm_requests, device):
             "peak_reserved_bytes": stats["peak_reserved_bytes"]}
 
 
+def run_c3(pkg, device, reps=3):
+    """Configuration 3: 64 streams x 2^20 complex64, P=4096, T=16, Blackman; every
+    DFT path as one batched launch over the 64 streams; rel. L2 on sampled spectra."""
+    import numpy as np
+    import torch
+    from paper_2408_16551_gb300 import synth
+    specs = synth.config_c3()
+    xs_host = [sp.generate() for sp in specs]
+    xs = [torch.from_numpy(x).to(device) for x in xs_host]
+    P, T, win = specs[0].P, specs[0].T, specs[0].window
+    n_total = sum(x.size for x in xs_host)
+    out = {"workload": "c3: 64 streams x 2^20 complex64 samples (CN(0,1) + 2 tones each), P=4096, T=16, "
+                       "Blackman-windowed sinc; one batched launch per DFT path", "n_samples": int(n_total)}
+    rows = [0, 120, 240]
+    for name, path in (("fft_f32", pkg.PFB_DFT_FFT_F32), ("gemm_bf16x3", pkg.PFB_DFT_GEMM_BF16X3),
+                       ("gemm_f32", pkg.PFB_DFT_GEMM_F32)):
+        try:
+            plan = pkg.Plan(P, T, pkg.PFB_IN_C64, win, path)
+            S = plan.out_spectra(xs_host[0].size)
+            outs = [torch.empty((S, P), dtype=torch.complex64, device=device) for _ in xs]
+            entries = [(plan, x, o) for x, o in zip(xs, outs)]
+            batch = pkg.Batch(entries)
+            batch.launch()
+            torch.cuda.synchronize()
+            r = 1 if path == pkg.PFB_DFT_GEMM_F32 else reps
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(r):
+                batch.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / r
+            errs = [sampled_rel_l2(outs[i], xs_host[i], pkg.PFB_IN_C64, P, T, win, rows) for i in (0, 37)]
+            out[name] = {"gsps": n_total / (ms * 1e-3) / 1e9, "ms": ms, "rel_l2": max(errs), "kernel": plan.kernel_name}
+            batch.close(); plan.close()
+            del outs
+        except pkg.PFBError as e:
+            out[name] = {"gsps": None, "unavailable": str(e)}
+    return out
+
+
+def run_c4(pkg, device, reps=5):
+    """Configuration 4: 256 uneven streams (P in {256,512,1024,4096}, T in {8,16},
+    lengths log-uniform 2^14..2^22) as one captured CUDA graph over per-variant
+    persistent launches, tile shapes from the autotuner."""
+    import torch
+    from paper_2408_16551_gb300 import synth
+    specs = synth.config_c4()
+    plans = {}
+    entries = []
+    n_total = 0
+    for sp in specs:
+        key = (sp.P, sp.T, sp.window)  # one plan per shape; streams of a shape share it
+        if key not in plans:
+            plans[key] = pkg.Plan(sp.P, sp.T, pkg.PFB_IN_C64, sp.window, pkg.PFB_DFT_FFT_F32)
+            plans[key].autotune(min(sp.P * 4096, 1 << 24))
+        plan = plans[key]
+        x = torch.from_numpy(sp.generate()).to(device)
+        S = plan.out_spectra(sp.n_samples)
+        o = torch.empty((max(S, 1), sp.P), dtype=torch.complex64, device=device)
+        entries.append((plan, x, o))
+        n_total += sp.n_samples
+    batch = pkg.Batch(entries)
+    batch.launch()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        batch.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    zero = sum(1 for (p, x, o) in entries if p.out_spectra(x.numel()) == 0)
+    return {"workload": "c4: 256 uneven complex64 streams, P~U{256,512,1024,4096}, T~U{8,16}, N=2^U, U~U(14,22); "
+                        "one CUDA graph of per-variant persistent launches, autotuned tile shapes",
+            "n_samples": int(n_total), "gsps": n_total / (ms * 1e-3) / 1e9, "ms": ms,
+            "streams_with_zero_spectra": zero}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,8 +383,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--no-configs", action="store_true", help="skip the c3/c4 lines")
     ap.add_argument("--minimal", action="store_true", help="headline timing only (for profiler runs)")
     ap.add_argument("--nsets", type=int, default=4, help="rotating input/output buffer sets")
+    ap.add_argument("--variant", type=int, default=-1, help="kernel variant of the FFT path (-1: autotune)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -333,7 +414,10 @@ def main():
     n = int(x.size)
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_FFT_F32)
     S = plan.out_spectra(n)
-    tune_ms = plan.autotune(n) if not args.minimal else None  # tile shape from the autotuner
+    if args.variant >= 0:
+        plan.variant = args.variant
+    else:
+        plan.autotune(n)  # tile shape (kernel variant) from the autotuner
     nsets = max(1, args.nsets)  # rotating input/output sets: 4 x 256 MiB > 129 MB L2
     xd0 = torch.from_numpy(x).to(device)
     xs = [xd0] + [xd0.clone() for _ in range(nsets - 1)]
@@ -380,10 +464,12 @@ def main():
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     traffic = None
     prof = load_json(os.path.join(ROOT, "profiles", "traffic.json"))
-    if prof and prof.get("source_hash") == source_hash() and plan.kernel_name in prof.get("kernels", {}):
-        traffic = prof["kernels"][plan.kernel_name].get("dram_bytes_per_launch")
+    kkey = f"{plan.kernel_name}:{plan.variant}"
+    if prof and prof.get("source_hash") == source_hash() and kkey in prof.get("kernels", {}):
+        traffic = prof["kernels"][kkey].get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": plan.kernel_name, "algorithmic_bytes_per_launch": alg_bytes,
+                "traffic": traffic, "kernel": f"{plan.kernel_name} variant {plan.variant}",
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     line = {
@@ -437,6 +523,12 @@ def main():
             dt = (time.perf_counter() - t0) / k2
             line["e2e"] = {"value": n / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * 8,
                            "d2h_bytes_per_step": S * P * 8, "api": "pfb_execute_host (pinned host buffers)"}
+
+        if not args.no_configs and rank == 0:
+            del xs, outs
+            torch.cuda.empty_cache()
+            line["c3"] = run_c3(pkg, device)
+            line["c4"] = run_c4(pkg, device)
 
         if not args.no_serving and rank == 0:
             try:

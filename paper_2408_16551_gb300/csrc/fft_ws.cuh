@@ -23,6 +23,9 @@
 // For P = 1024 (4 branches per FIR thread, 16 taps) the FIR warpgroups take
 // 208 registers, the FFT warpgroup 72 and the producer warpgroup 24
 // (setmaxnreg): 256*208 + 128*72 + 128*24 = 512*128 registers at launch.
+// Thread t of the FIR warps owns the branch pairs (2t, 2t+1) + k*P/NPAIR, so
+// its ring reads and branch-sum writes are contiguous across the warp (no
+// shared-memory bank conflicts).
 #pragma once
 
 #include "devutil.cuh"
@@ -35,6 +38,7 @@ namespace pfb {
 template <int P, int TT, int IN>
 struct WsCfg {
     static constexpr int NB = P >= 1024 ? 4 : (P >= 512 ? 2 : 1);  // branches per FIR thread
+    static constexpr int NPAIR = NB >= 2 ? NB / 2 : 1;              // branch pairs (2t, 2t+1) + k P/NPAIR
     static constexpr int NFT = P / NB;                               // FIR threads
     static constexpr int NFIRW = NFT / 32;
     static constexpr bool SETMAXNREG = (P >= 1024);
@@ -196,7 +200,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
         // ======================= FIR warps =======================
         if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
         const int t = threadIdx.x;
-        const int q0 = NB * t;
+        constexpr int NPAIR = C::NPAIR;
+        constexpr int PSTRIDE = P / NPAIR;   // distance between this thread's branch pairs
+        // branch of (pair k, b): k * PSTRIDE + 2t + b   (NB = 1: branch t)
+        auto branch = [&](int k, int b) { return NB == 1 ? t : k * PSTRIDE + 2 * t + b; };
         float h[TT][NB];
         float2 pend[TT][NB];
         int cur = -1;
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
 #pragma unroll
                 for (int m = 0; m < TT; ++m)
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) h[m][b] = __ldg(d.taps + m * P + q0 + b);
+                    for (int b = 0; b < NB; ++b) h[m][b] = __ldg(d.taps + m * P + branch(b >> 1, b & 1));
             }
             const int64_t nspec = sB - sA;
             const int64_t nfr = nspec + TT - 1;
@@ -236,29 +243,32 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                         for (int b = 0; b < NB; ++b) v[b] = make_float2(0.f, 0.f);
                         if (ok) {
                             const uint8_t *fr = ring + slot * C::FB;
-                            float sc = d.scale;
-                            if constexpr (IN == PFB_IN_C64) {
-                                const float4 *p4 = reinterpret_cast<const float4 *>(fr) + (q0 >> 1);
+                            const float sc = d.scale;
 #pragma unroll
-                                for (int b2 = 0; b2 < (NB + 1) / 2; ++b2) {
-                                    if (NB == 1) {
-                                        v[0] = reinterpret_cast<const float2 *>(fr)[q0];
-                                    } else {
-                                        const float4 w4 = p4[b2];
-                                        v[2 * b2] = make_float2(w4.x, w4.y);
-                                        v[2 * b2 + 1] = make_float2(w4.z, w4.w);
+                            for (int k2 = 0; k2 < NPAIR; ++k2) {
+                                if constexpr (NB == 1) {
+                                    if constexpr (IN == PFB_IN_C64) v[0] = reinterpret_cast<const float2 *>(fr)[t];
+                                    else if constexpr (IN == PFB_IN_R32)
+                                        v[0] = make_float2(reinterpret_cast<const float *>(fr)[t], 0.f);
+                                    else {
+                                        const char2 c2 = reinterpret_cast<const char2 *>(fr)[t];
+                                        v[0] = make_float2((float)c2.x * sc, (float)c2.y * sc);
                                     }
-                                }
-                            } else if constexpr (IN == PFB_IN_R32) {
-                                const float *pf = reinterpret_cast<const float *>(fr) + q0;
-#pragma unroll
-                                for (int b = 0; b < NB; ++b) v[b] = make_float2(pf[b], 0.f);
-                            } else {
-                                const char2 *pc2 = reinterpret_cast<const char2 *>(fr) + q0;
-#pragma unroll
-                                for (int b = 0; b < NB; ++b) {
-                                    const char2 c2 = pc2[b];
-                                    v[b] = make_float2((float)c2.x * sc, (float)c2.y * sc);
+                                } else {
+                                    const int q = branch(k2, 0);   // even branch of the pair
+                                    if constexpr (IN == PFB_IN_C64) {
+                                        const float4 w4 = reinterpret_cast<const float4 *>(fr)[q >> 1];
+                                        v[2 * k2] = make_float2(w4.x, w4.y);
+                                        v[2 * k2 + 1] = make_float2(w4.z, w4.w);
+                                    } else if constexpr (IN == PFB_IN_R32) {
+                                        const float2 w2 = reinterpret_cast<const float2 *>(fr)[q >> 1];
+                                        v[2 * k2] = make_float2(w2.x, 0.f);
+                                        v[2 * k2 + 1] = make_float2(w2.y, 0.f);
+                                    } else {
+                                        const char4 c4 = reinterpret_cast<const char4 *>(fr)[q >> 1];
+                                        v[2 * k2] = make_float2((float)c4.x * sc, (float)c4.y * sc);
+                                        v[2 * k2 + 1] = make_float2((float)c4.z * sc, (float)c4.w * sc);
+                                    }
                                 }
                             }
                             __syncwarp();
@@ -293,9 +303,9 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                                 first_row_spec = jspec;
                             }
                             if (!ok) break;
-                            float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW + ypad<G>(q0);
+                            float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW;
 #pragma unroll
-                            for (int b = 0; b < NB; ++b) yrow[b] = pend[jslot][b];
+                            for (int b = 0; b < NB; ++b) yrow[ypad<G>(branch(b >> 1, b & 1))] = pend[jslot][b];
                             ++brow;
                             if (brow == SB || jspec == nspec - 1) {
                                 if (t == 0) {
