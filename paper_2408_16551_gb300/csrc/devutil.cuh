@@ -66,6 +66,16 @@ __device__ __forceinline__ float2 csub2(float2 a, float2 b) {
     return d;
 }
 
+// packed fp32x2 fused multiply-add: d = a * b + c on both lanes
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tmov.b64 rc, {%6,%7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 template <int R>
 __device__ __forceinline__ constexpr int bitrev(int i) {
     int r = 0;

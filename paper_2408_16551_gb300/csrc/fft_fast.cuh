@@ -36,16 +36,6 @@ namespace pfb {
 template <int G>
 __device__ __forceinline__ int ypad(int i) { return i + i / G; }
 
-// packed fp32x2 arithmetic (Blackwell): two lanes of fp32 per instruction
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tmov.b64 rc, {%6,%7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0,%1}, rd;}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-
 }  // namespace pfb
 
 #include "fft_ws.cuh"

@@ -10,13 +10,16 @@
 // (hi = RN(v), lo = RN(v - hi); B from its FP64 value, y from its fp32 value)
 // and three products are accumulated in FP32:  hi*hi + hi*lo + lo*hi.
 //
-// CTA = 5 warps, one CTA per SM (all 512 TMEM columns):
-//   warps 0-3: the FIR of Sec. 5.2 for a 128-spectrum x 32-branch slice per
-//              K block (lane = branch, register window over 32 spectra,
-//              coalesced loads), a warp-local transpose through shared memory
+// CTA = 9 warps, one CTA per SM (all 512 TMEM columns):
+//   warps 0-7: the FIR of Sec. 5.2 for a 128-spectrum x 32-branch slice per
+//              K block: warp w covers the 32 spectra of TMEM lane quarter w%4
+//              and 16 of the 32 branches (w/4); lane = (branch, half of the
+//              spectra), register window over 16 spectra, packed fp32x2 FMAs,
+//              coalesced loads; a warp-local transpose through shared memory
 //              to lane = spectrum, the hi/lo split, tcgen05.st into the A stage
-//              in TMEM; after the K loop, the epilogue (tcgen05.ld -> HBM);
-//   warp 4:    lane 0 bulk-copies the pre-tiled B_hi/B_lo tiles of the K block
+//              in TMEM; the accumulator drains and the epilogue (tcgen05.ld ->
+//              HBM) are split the same way (column halves);
+//   warp 8:    lane 0 bulk-copies the pre-tiled B_hi/B_lo tiles of the K block
 //              into shared memory (mbarrier complete_tx) and issues the
 //              3 x 4 tcgen05.mma (M=128, N=256, K=16, A from TMEM, B from
 //              shared memory, no swizzle) and the tcgen05.commit.
@@ -38,12 +41,12 @@
 namespace pfb {
 
 constexpr int K2_M = 128, K2_N = 256, K2_KB = 64;  // reals per tile: M rows, N cols, K block
-constexpr int K2_WARPS = 5, K2_THREADS = K2_WARPS * 32;
+constexpr int K2_FIRW = 8, K2_WARPS = K2_FIRW + 1, K2_THREADS = K2_WARPS * 32;
 constexpr int K2_TILE_ELEMS = K2_N * K2_KB;  // bf16 elements per B tile (32 KB)
 constexpr int K2_TILE_BYTES = K2_TILE_ELEMS * 2;
 constexpr int K2_SMEM_B = 2 * 2 * K2_TILE_BYTES;  // 2 stages x (hi, lo)
-constexpr int K2_TR = 33;                          // transpose row stride (float2)
-constexpr int K2_SMEM_TR = 4 * 32 * K2_TR * 8;
+constexpr int K2_TR = 17;                          // transpose row stride (float2)
+constexpr int K2_SMEM_TR = K2_FIRW * 32 * K2_TR * 8;
 constexpr int K2_SMEM_BAR = 64;
 constexpr int K2_SMEM = K2_SMEM_B + K2_SMEM_TR + K2_SMEM_BAR + 1024;  // + alignment slack
 constexpr uint32_t K2_TMEM_COLS = 512;
@@ -173,6 +176,16 @@ __device__ __forceinline__ void tmem_st32<32>(uint32_t taddr, const uint32_t (&v
         : "memory");
 }
 
+template <>
+__device__ __forceinline__ void tmem_st32<16>(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -187,11 +200,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
 
-// Move this thread's accumulator row (256 fp32 columns of TMEM) into the
-// output tile row: first chunk stores, later chunks add (FP32, RN).
+// Move 128 columns (this warp's half) of this thread's accumulator row into
+// the output tile row: first chunk stores, later chunks add (FP32, RN).
 __device__ __forceinline__ void drain_row(uint32_t trow, float *orow, bool valid, bool first, bool last) {
 #pragma unroll 1
-    for (int c = 0; c < K2_N / 32; ++c) {
+    for (int c = 0; c < K2_N / 64; ++c) {
         uint32_t r[32];
         tmem_ld32(trow + 32 * c, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
-    if (warp == 4) {
+    if (warp == K2_FIRW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void *)tmem_slot)),
                      "r"(K2_TMEM_COLS)
@@ -266,7 +279,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
             const uint32_t stage = g & 1;
             const bool need_wait = g >= 2;
             const uint32_t wpar = ((g >> 1) + 1) & 1;  // completion (g-2)/2 of mdone[stage]
-            if (warp == 4) {
+            if (warp == K2_FIRW) {
                 if (lane == 0) {
                     if (need_wait && !mbar_wait(mdone0 + 8 * stage, wpar)) {
                         *abort_flag = 1;
@@ -296,32 +309,31 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                 if (!ok) *abort_flag = 1;
                 tc_fence_after();
                 if (ok) {
-                    const int p = kb * 32 + lane;           // this lane's branch
-                    const int64_t f0 = s0 + 32 * warp;      // first frame of the window
+                    const int q = warp & 3, hb = warp >> 2;      // lane quarter, branch half
+                    const int bl = lane & 15, rh = lane >> 4;    // branch in the half, spectra half
+                    const int p = kb * 32 + 16 * hb + bl;        // this lane's branch
+                    const int64_t f0 = s0 + 32 * q + 16 * rh;    // first frame of the window
                     float h[TT];
 #pragma unroll
                     for (int m = 0; m < TT; ++m) h[m] = __ldg(d.taps + m * P + p);
-                    float2 acc[32];
+                    float2 acc[16];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] = make_float2(0.f, 0.f);
-                    const bool interior = f0 >= d.n_state && f0 + 32 + TT - 1 <= d.n_frames;
+                    for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+                    const bool interior = f0 >= d.n_state && f0 + 16 + TT - 1 <= d.n_frames;
                     if (interior) {
                         const int64_t base = (f0 - d.n_state) * P + p;
 #pragma unroll
-                        for (int i = 0; i < 32 + TT - 1; ++i) {
+                        for (int i = 0; i < 16 + TT - 1; ++i) {
                             const float2 v = Loader<IN>::load1(d.in, base + (int64_t)i * P, d.scale);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
+                            for (int j = 0; j < 16; ++j) {
                                 const int m = i - j;
-                                if (m >= 0 && m < TT) {
-                                    acc[j].x = fmaf(h[m], v.x, acc[j].x);
-                                    acc[j].y = fmaf(h[m], v.y, acc[j].y);
-                                }
+                                if (m >= 0 && m < TT) acc[j] = fma2(make_float2(h[m], h[m]), v, acc[j]);
                             }
                         }
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 32 + TT - 1; ++i) {
+                        for (int i = 0; i < 16 + TT - 1; ++i) {
                             const int64_t f = f0 + i;
                             float2 v = make_float2(0.f, 0.f);
                             if (f < d.n_frames) {
@@ -330,23 +342,20 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                                 v = Loader<IN>::load1(src, smp + p, d.scale);
                             }
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
+                            for (int j = 0; j < 16; ++j) {
                                 const int m = i - j;
-                                if (m >= 0 && m < TT) {
-                                    acc[j].x = fmaf(h[m], v.x, acc[j].x);
-                                    acc[j].y = fmaf(h[m], v.y, acc[j].y);
-                                }
+                                if (m >= 0 && m < TT) acc[j] = fma2(make_float2(h[m], h[m]), v, acc[j]);
                             }
                         }
                     }
-                    // transpose: lane = branch -> lane = spectrum row
+                    // transpose: lane = (branch, spectra half) -> lane = spectrum row
                     float2 *tr = tr_all + warp * 32 * K2_TR;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) tr[j * K2_TR + lane] = acc[j];
+                    for (int j = 0; j < 16; ++j) tr[(16 * rh + j) * K2_TR + bl] = acc[j];
                     __syncwarp();
-                    uint32_t vh[32], vl[32];
+                    uint32_t vh[16], vl[16];
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
+                    for (int c = 0; c < 16; ++c) {
                         const float2 y = tr[lane * K2_TR + c];
                         const __nv_bfloat162 hi = __floats2bfloat162_rn(y.x, y.y);
                         const float2 hf = __bfloat1622float2(hi);
@@ -355,10 +364,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                         vl[c] = bf16x2_bits(lo);
                     }
                     __syncwarp();
-                    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-                    const uint32_t acol = K2_COL_A + 64 * stage;
-                    tmem_st32<32>(trow + acol, vh);
-                    tmem_st32<32>(trow + acol + 32, vl);
+                    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+                    const uint32_t acol = K2_COL_A + 64 * stage + 16 * hb;
+                    tmem_st32<16>(trow + acol, vh);
+                    tmem_st32<16>(trow + acol + 32, vl);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     if (kb > 0 && kb % K2_CHUNK == 0) {
                         // chunk boundary: the previous K block's MMAs end the chunk; move the
@@ -368,10 +377,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                         if (!ok) *abort_flag = 1;
                         tc_fence_after();
                         if (ok) {
-                            const int row = 32 * warp + lane;
+                            const int row = 32 * q + lane;
                             const int64_t s = s0 + row;
                             float *orow = reinterpret_cast<float *>(d.out) + s * 2 * (int64_t)P + (int64_t)nt * K2_N;
-                            drain_row(trow, orow, s < d.S, kb == K2_CHUNK, false);
+                            drain_row(trow + 128 * hb, orow + 128 * hb, s < d.S, kb == K2_CHUNK, false);
                         }
                     }
                 }
@@ -382,7 +391,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                 aborted = true;
                 break;
             }
-            if (warp == 4 && lane == 0) {
+            if (warp == K2_FIRW && lane == 0) {
                 tc_fence_after();
                 if (!mbar_wait(bfull0 + 8 * stage, (g >> 1) & 1)) {
                     *abort_flag = 1;
@@ -407,17 +416,18 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
         }
         if (aborted) break;
         // ---------------- epilogue: accumulator -> HBM ----------------
-        if (warp < 4) {
+        if (warp < K2_FIRW) {
+            const int q = warp & 3, hb = warp >> 2;
             const uint32_t gl = g - 1;
             bool ok = mbar_wait(mdone0 + 8 * (gl & 1), (gl >> 1) & 1);
             if (!ok) *abort_flag = 1;
             tc_fence_after();
             if (ok) {
-                const int row = 32 * warp + lane;
+                const int row = 32 * q + lane;
                 const int64_t s = s0 + row;
                 float *orow = reinterpret_cast<float *>(d.out) + s * 2 * (int64_t)P + (int64_t)nt * K2_N;
-                const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-                drain_row(trow, orow, s < d.S, KBLK <= K2_CHUNK, true);
+                const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+                drain_row(trow + 128 * hb, orow + 128 * hb, s < d.S, KBLK <= K2_CHUNK, true);
             }
             tc_fence_before();
         }
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
 
     // ---------------- teardown ----------------
     __syncthreads();
-    if (warp == 4) {
+    if (warp == K2_FIRW) {
         if (lane == 0) {
             bool ok = true;
             if (last_commit >= 0) ok = mbar_wait(mdone0 + 8 * (last_commit & 1), (last_commit >> 1) & 1) && ok;
