@@ -353,6 +353,7 @@ static pfb_status launch_fft_fast_v(int variant, LaunchArgs &a, cudaStream_t str
     pfb_status launch_fft_fast_p<PV>(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {               \
         const int v = plan.variant;                                                                        \
         a.tw = (v == 4) ? plan.d_tw32 : plan.d_tw;                                                         \
+        a.aux = plan.d_tw_r2;                                                                              \
         switch (plan.in_dtype * 100 + plan.TT) {                                                           \
         case PFB_IN_C64 * 100 + 4: return launch_fft_fast_v<PV, 4, PFB_IN_C64>(v, a, stream);              \
         case PFB_IN_C64 * 100 + 8: return launch_fft_fast_v<PV, 8, PFB_IN_C64>(v, a, stream);              \

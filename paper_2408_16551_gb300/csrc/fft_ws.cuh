@@ -8,7 +8,8 @@
 // One CTA per SM walks a contiguous range of spectra.  Its warps have roles:
 //   producer (1 warp, lane 0): 1-D bulk copies of whole input frames into a
 //       ring of NSLOT shared-memory slots (mbarrier complete_tx), in frame
-//       order, so every input byte is read from HBM exactly once per CTA;
+//       order, so every input byte is read from HBM exactly once per CTA
+//       (an L2 prefetch running ahead of the ring measured slower);
 //   FIR warps (P/NB threads, NB consecutive branches each): stream the frames
 //       out of the ring; the branch sums of the T spectra a frame feeds live in
 //       registers (slot (s mod T), rotated at compile time by unrolling the
@@ -35,10 +36,20 @@
 
 namespace pfb {
 
+#ifndef PFB_WS_DIF4
+#define PFB_WS_DIF4 1
+#endif
+
 template <int P, int TT, int IN>
 struct WsCfg {
     static constexpr int NB = P >= 1024 ? 4 : (P >= 512 ? 2 : 1);  // branches per FIR thread
     static constexpr int NPAIR = NB >= 2 ? NB / 2 : 1;              // branch pairs (2t, 2t+1) + k P/NPAIR
+    // P = 1024: thread t owns branches t + k*P/4 and applies the first radix-4
+    // decimation-in-frequency step (with its twiddles) before handing over, so
+    // the FFT warps run four P/4-point transforms per spectrum
+    static constexpr bool DIF4 = PFB_WS_DIF4 && (P == 1024);
+    static constexpr int Q = P / 4;                                  // sub-transform length (DIF4)
+    static constexpr int SROW = Q + Q / 16 + 8;                      // sub-row stride (float2), 16 banks apart
     static constexpr int NFT = P / NB;                               // FIR threads
     static constexpr int NFIRW = NFT / 32;
     static constexpr bool SETMAXNREG = (P >= 1024);
@@ -54,19 +65,22 @@ struct WsCfg {
     static constexpr int NSLOT = 8;
     static constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
     static constexpr int FB = P * ESZ;                               // frame bytes
-    static constexpr int NTW = fft_tw_entries(P, MR);
-    static constexpr int NPASS = fft_npasses(P, MR);
-    // shared memory layout (bytes)
+    // pass twiddles: the P-point list, or (DIF4) the Q-point list, which is a
+    // prefix of the P-point table, followed by w_P^(t k), k = 1..3, t < Q
+    static constexpr int NTW = DIF4 ? fft_tw_entries(Q, MR) + 3 * Q : fft_tw_entries(P, MR);
+    static constexpr int NPASS = DIF4 ? fft_npasses(Q, MR) : fft_npasses(P, MR);
+    // shared memory layout (bytes); DIF4 needs one W buffer (two passes)
     static constexpr int OFF_RING = 0;
     static constexpr int OFF_Y = OFF_RING + NSLOT * FB;
-    static constexpr int YBUF = SB * YROW * 8;
+    static constexpr int YBUF = DIF4 ? SB * 4 * SROW * 8 : SB * YROW * 8;
     static constexpr int OFF_W = OFF_Y + 2 * YBUF;
-    static constexpr int OFF_TW = OFF_W + 2 * YBUF;
+    static constexpr int OFF_TW = OFF_W + (DIF4 ? 1 : 2) * YBUF;
     static constexpr int OFF_META = OFF_TW + (NTW > 0 ? NTW : 1) * 8;
     static constexpr int OFF_BAR = OFF_META + 3 * 32;
     static constexpr int NBAR = 2 * NSLOT + 4;
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
     static_assert(NFT % 128 == 0 || !SETMAXNREG, "FIR warps form whole warpgroups");
+    static_assert(!DIF4 || (NB == 4 && NFT == Q && fft_npasses(Q, MR) == 2), "DIF4 layout");
     static_assert(NFIRW * 32 + NFFTT + (SETMAXNREG ? 128 : 32) == NTHREADS, "layout");
     // register split (setmaxnreg): FIR 208, FFT 72, producer warpgroup 24
     static_assert(!SETMAXNREG || NFT * 208 + NFFTT * 72 + 128 * 24 <= NTHREADS * (65536 / NTHREADS), "registers");
@@ -146,6 +160,43 @@ __device__ __forceinline__ void ws_passes(float2 *Y, float2 *W0, float2 *W1, con
     }
 }
 
+// Last pass of the four Q-point sub-transforms of each spectrum (DIF4): sub-
+// transform k1 of row `row` sits at sub-row 4*row + k1; its bin m is the
+// spectrum's bin 4m + k1.  k1 varies fastest across threads, so each store
+// instruction writes 32 consecutive bins.
+template <int Q, int SB, int SROW, int G>
+__device__ __forceinline__ void ws_dif4_last(const float2 *src, const float2 *tw, float2 *out_row0, int nrows, int ft,
+                                             int nft) {
+    constexpr int MR = 16;
+    constexpr int PASS = fft_npasses(Q, MR) - 1;
+    constexpr int R = fft_radix(Q, PASS, MR);
+    constexpr int NS = fft_ns(Q, PASS, MR);
+    constexpr int STRIDE = Q / R;
+    static_assert(STRIDE == NS && STRIDE % G == 0, "last pass");
+    constexpr int NBF = SB * 4 * STRIDE;
+    constexpr int P = 4 * Q;
+    const float2 *twp = tw + fft_tw_offset(Q, PASS, MR);
+#pragma unroll 1
+    for (int b = ft; b < NBF; b += nft) {
+        const int k1 = b & 3;
+        const int j = (b >> 2) % STRIDE;
+        const int row = (b >> 2) / STRIDE;
+        const float2 *s = src + (4 * row + k1) * SROW + ypad<G>(j);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[r * (STRIDE + STRIDE / G)];
+        const float2 *w = twp + j * (R - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
+        dft_reg<R, true>(v);
+        if (row < nrows) {
+            float2 *o = out_row0 + row * P + 4 * j + k1;
+#pragma unroll
+            for (int r = 0; r < R; ++r) store_cs(o + 4 * NS * r, v[r]);
+        }
+    }
+}
+
 // iterate the CTA's spectra range as (stream, [sA, sB)) segments
 struct WsRange {
     int64_t u, u1;
@@ -190,6 +241,19 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
         mbar_init_fence();
         *abort_flag = 0;
     }
+    // twiddle tables into shared memory (all threads, before the roles split)
+    if constexpr (C::DIF4) {
+        constexpr int NTQ = fft_tw_entries(C::Q, C::MR);
+        const float2 *tw_half = static_cast<const float2 *>(a.aux);  // w_P^r, r < P/2
+        for (int i = threadIdx.x; i < NTQ; i += C::NTHREADS) tw[i] = a.tw[i];
+        for (int i = threadIdx.x; i < 3 * C::Q; i += C::NTHREADS) {
+            const int r = (i / C::Q + 1) * (i % C::Q);  // w_P^(t k1), t = i mod Q, k1 = i / Q + 1
+            const float2 w = tw_half[r % (P / 2)];
+            tw[NTQ + i] = r < P / 2 ? w : make_float2(-w.x, -w.y);
+        }
+    } else {
+        for (int i = threadIdx.x; i < C::NTW; i += C::NTHREADS) tw[i] = a.tw[i];
+    }
     __syncthreads();
 
     WsRange range;
@@ -203,7 +267,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
         constexpr int NPAIR = C::NPAIR;
         constexpr int PSTRIDE = P / NPAIR;   // distance between this thread's branch pairs
         // branch of (pair k, b): k * PSTRIDE + 2t + b   (NB = 1: branch t)
-        auto branch = [&](int k, int b) { return NB == 1 ? t : k * PSTRIDE + 2 * t + b; };
+        auto branch = [&](int k, int b) {
+            if constexpr (C::DIF4) return (2 * k + b) * C::Q + t;
+            else return NB == 1 ? t : k * PSTRIDE + 2 * t + b;
+        };
         float h[TT][NB];
         float2 pend[TT][NB];
         int cur = -1;
@@ -246,7 +313,19 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                             const float sc = d.scale;
 #pragma unroll
                             for (int k2 = 0; k2 < NPAIR; ++k2) {
-                                if constexpr (NB == 1) {
+                                if constexpr (C::DIF4) {
+#pragma unroll
+                                    for (int b = 0; b < 2; ++b) {
+                                        const int q = branch(k2, b);
+                                        if constexpr (IN == PFB_IN_C64) v[2 * k2 + b] = reinterpret_cast<const float2 *>(fr)[q];
+                                        else if constexpr (IN == PFB_IN_R32)
+                                            v[2 * k2 + b] = make_float2(reinterpret_cast<const float *>(fr)[q], 0.f);
+                                        else {
+                                            const char2 c2 = reinterpret_cast<const char2 *>(fr)[q];
+                                            v[2 * k2 + b] = make_float2((float)c2.x * sc, (float)c2.y * sc);
+                                        }
+                                    }
+                                } else if constexpr (NB == 1) {
                                     if constexpr (IN == PFB_IN_C64) v[0] = reinterpret_cast<const float2 *>(fr)[t];
                                     else if constexpr (IN == PFB_IN_R32)
                                         v[0] = make_float2(reinterpret_cast<const float *>(fr)[t], 0.f);
@@ -303,9 +382,24 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                                 first_row_spec = jspec;
                             }
                             if (!ok) break;
-                            float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW;
+                            if constexpr (C::DIF4) {
+                                // radix-4 DIF step on y[t + k Q], k = 0..3, then z_k1 *= w_P^(t k1)
+                                float2 *ysub = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF) +
+                                               brow * 4 * C::SROW + ypad<G>(t);
+                                const float2 a0 = cadd(pend[jslot][0], pend[jslot][2]);
+                                const float2 a1 = csub(pend[jslot][0], pend[jslot][2]);
+                                const float2 a2 = cadd(pend[jslot][1], pend[jslot][3]);
+                                const float2 a3 = csub(pend[jslot][1], pend[jslot][3]);
+                                const float2 *tw4 = tw + fft_tw_entries(C::Q, C::MR) + t;
+                                ysub[0] = cadd(a0, a2);
+                                ysub[C::SROW] = cmul(make_float2(a1.x + a3.y, a1.y - a3.x), tw4[0]);
+                                ysub[2 * C::SROW] = cmul(csub(a0, a2), tw4[C::Q]);
+                                ysub[3 * C::SROW] = cmul(make_float2(a1.x - a3.y, a1.y + a3.x), tw4[2 * C::Q]);
+                            } else {
+                                float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW;
 #pragma unroll
-                            for (int b = 0; b < NB; ++b) yrow[ypad<G>(branch(b >> 1, b & 1))] = pend[jslot][b];
+                                for (int b = 0; b < NB; ++b) yrow[ypad<G>(branch(b >> 1, b & 1))] = pend[jslot][b];
+                            }
                             ++brow;
                             if (brow == SB || jspec == nspec - 1) {
                                 if (t == 0) {
@@ -326,8 +420,6 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
         // ======================= FFT warps =======================
         if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
         const int ft = threadIdx.x - C::NFT;
-        for (int i = ft; i < C::NTW; i += C::NFFTT) tw[i] = a.tw[i];
-        named_bar_sync<1>(C::NFFTT);
         uint32_t bc = 0;
         bool ok = true;
         int si;
@@ -346,8 +438,16 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                 }
                 const WsMeta mt = meta[bc & 1];
                 float2 *Yb = Y + (bc & 1) * (SB * YROW);
-                ws_passes<P, C::MR, SB, 0, YROW, G>(Yb, W, W + SB * YROW, tw, mt.out, mt.nrows, ft, C::NFFTT,
-                                                    yempty0 + 8 * (bc & 1), C::NFFTT);
+                if constexpr (C::DIF4) {
+                    Yb = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF);
+                    ws_pass<C::Q, C::MR, 4 * SB, 0, false, C::SROW, G>(Yb, W, tw, nullptr, 0, ft, C::NFFTT);
+                    named_bar_sync<1>(C::NFFTT);
+                    if (ft == 0) mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
+                    ws_dif4_last<C::Q, SB, C::SROW, G>(W, tw, mt.out, mt.nrows, ft, C::NFFTT);
+                } else {
+                    ws_passes<P, C::MR, SB, 0, YROW, G>(Yb, W, W + SB * YROW, tw, mt.out, mt.nrows, ft, C::NFFTT,
+                                                        yempty0 + 8 * (bc & 1), C::NFFTT);
+                }
                 named_bar_sync<1>(C::NFFTT);  // W buffers free before the next batch
             }
         }
@@ -362,6 +462,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
             while (ok && ws_next_segment(a, range, si, sA, sB)) {
                 const StreamDesc &d = a.s[si];
                 const int64_t f_end = sB + TT - 1;
+                const uint8_t *in = static_cast<const uint8_t *>(d.in);
                 for (int64_t f = sA; f < f_end && ok; ++f, ++pc) {
                     const uint32_t slot = pc % NSLOT;
                     if (pc >= NSLOT && !mbar_wait(empty0 + 8 * slot, ((pc / NSLOT) + 1) & 1)) {
@@ -371,7 +472,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                     }
                     const uint8_t *src;
                     if (f < d.n_state) src = static_cast<const uint8_t *>(d.state) + f * (int64_t)C::FB;
-                    else src = static_cast<const uint8_t *>(d.in) + (f - d.n_state) * (int64_t)C::FB;
+                    else src = in + (f - d.n_state) * (int64_t)C::FB;
                     mbar_expect_tx(full0 + 8 * slot, C::FB);
                     bulk_g2s(smem_u32(ring + slot * C::FB), src, C::FB, full0 + 8 * slot);
                 }

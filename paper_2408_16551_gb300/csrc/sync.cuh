@@ -52,6 +52,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// L2 prefetch of `bytes` (multiple of 16, 16-byte aligned address) of global memory
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 template <int ID>
 __device__ __forceinline__ void named_bar_sync(int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(nthreads) : "memory");
