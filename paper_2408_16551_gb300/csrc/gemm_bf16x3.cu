@@ -37,6 +37,7 @@
 
 #include "devutil.cuh"
 #include "internal.h"
+#include "sync.cuh"
 
 namespace pfb {
 
@@ -118,29 +119,6 @@ pfb_status build_gemm_tables(Plan &plan) {
 // ---------------------------------------------------------------------------
 // PTX helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// bounded wait for the completion of the mbarrier phase with the given parity
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t t0 = globaltimer();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (globaltimer() - t0 > 1000000000ull) return false;
-    }
-}
-
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     // start address, LBO = 128 B (K direction), SBO = 1024 B (N direction),
     // version 1 (bit 46), no swizzle

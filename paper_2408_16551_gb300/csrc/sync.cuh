@@ -30,16 +30,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 
 // Bounded wait for the completion of the phase with the given parity: gives
 // up after `ns` nanoseconds of %globaltimer and returns false.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// (the timer is read only once the first try has failed)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t ns = 1000000000ull) {
+    if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(bar, parity)) return true;
         if (globaltimer() - t0 > ns) return false;
     }
 }
