@@ -16,7 +16,7 @@
 //       frame loop T times), so each frame costs T fp32x2 FMAs per branch and
 //       one spectrum of branch sums completes per frame; rows go to a
 //       double-buffered batch buffer Y in shared memory (SB spectra);
-//   FFT warps (96 threads): radix-16 Stockham passes, out of place
+//   FFT warps (128 threads): radix-16 Stockham passes, out of place
 //       (Y -> W0 -> W1 -> HBM), natural-order bins stored straight from
 //       registers; they release Y as soon as the first pass has read it.
 // Roles hand over through mbarriers; every wait is bounded (1 s of
@@ -24,9 +24,13 @@
 // For P = 1024 (4 branches per FIR thread, 16 taps) the FIR warpgroups take
 // 208 registers, the FFT warpgroup 72 and the producer warpgroup 24
 // (setmaxnreg): 256*208 + 128*72 + 128*24 = 512*128 registers at launch.
-// Thread t of the FIR warps owns the branch pairs (2t, 2t+1) + k*P/NPAIR, so
-// its ring reads and branch-sum writes are contiguous across the warp (no
-// shared-memory bank conflicts).
+// P = 1024 splits the DFT once more (decimation in frequency by 4): FIR thread
+// t owns branches t + k*P/4 (k = 0..3) and hands over the radix-4 butterfly
+// of its four branch sums; the FFT warps multiply by w_P^(t k1) in their
+// first pass and finish four P/4-point transforms (Y -> W -> HBM), bin
+// 4m + k1 coming from sub-transform k1.  Otherwise thread t owns the branch
+// pairs (2t, 2t+1) + k*P/NPAIR.  Either way its ring reads and branch-sum
+// writes are contiguous across the warp (no shared-memory bank conflicts).
 #pragma once
 
 #include "devutil.cuh"
@@ -45,8 +49,9 @@ struct WsCfg {
     static constexpr int NB = P >= 1024 ? 4 : (P >= 512 ? 2 : 1);  // branches per FIR thread
     static constexpr int NPAIR = NB >= 2 ? NB / 2 : 1;              // branch pairs (2t, 2t+1) + k P/NPAIR
     // P = 1024: thread t owns branches t + k*P/4 and applies the first radix-4
-    // decimation-in-frequency step (with its twiddles) before handing over, so
-    // the FFT warps run four P/4-point transforms per spectrum
+    // decimation-in-frequency butterfly before handing over; the FFT warps
+    // apply its twiddles in their first pass and run four P/4-point
+    // transforms per spectrum
     static constexpr bool DIF4 = PFB_WS_DIF4 && (P == 1024);
     static constexpr int Q = P / 4;                                  // sub-transform length (DIF4)
     static constexpr int SROW = Q + Q / 16 + 8;                      // sub-row stride (float2), 16 banks apart
@@ -93,9 +98,11 @@ struct WsMeta {
 };
 
 // one out-of-place Stockham pass over a batch of SB rows, run by the FFT warps
-template <int P, int MR, int SB, int PASS, bool LAST, int YROW, int G>
+// PRETW: rows are the DIF4 sub-rows (row mod 4 = k1) and element n of sub-row
+// k1 is first multiplied by pre[(k1 - 1) * P + n] = w_{4P}^(n k1) (k1 > 0)
+template <int P, int MR, int SB, int PASS, bool LAST, int YROW, int G, bool PRETW = false>
 __device__ __forceinline__ void ws_pass(const float2 *src, float2 *dst, const float2 *tw, float2 *out_row0, int nrows,
-                                        int ft, int nft) {
+                                        int ft, int nft, const float2 *pre = nullptr) {
     constexpr int R = fft_radix(P, PASS, MR);
     constexpr int NS = fft_ns(P, PASS, MR);
     constexpr int STRIDE = P / R;
@@ -113,6 +120,14 @@ __device__ __forceinline__ void ws_pass(const float2 *src, float2 *dst, const fl
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = s[ypad<G>(j + r * STRIDE)];
+        }
+        if constexpr (PRETW) {
+            const int k1 = row & 3;
+            if (k1 != 0) {
+                const float2 *w = pre + (k1 - 1) * P + j;
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = cmul(v[r], w[r * STRIDE]);
+            }
         }
         if constexpr (NS > 1) {
             const float2 *w = twp + (j % NS) * (R - 1);
@@ -383,18 +398,18 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                             }
                             if (!ok) break;
                             if constexpr (C::DIF4) {
-                                // radix-4 DIF step on y[t + k Q], k = 0..3, then z_k1 *= w_P^(t k1)
+                                // radix-4 DIF butterfly on y[t + k Q], k = 0..3
                                 float2 *ysub = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF) +
                                                brow * 4 * C::SROW + ypad<G>(t);
                                 const float2 a0 = cadd(pend[jslot][0], pend[jslot][2]);
                                 const float2 a1 = csub(pend[jslot][0], pend[jslot][2]);
                                 const float2 a2 = cadd(pend[jslot][1], pend[jslot][3]);
                                 const float2 a3 = csub(pend[jslot][1], pend[jslot][3]);
-                                const float2 *tw4 = tw + fft_tw_entries(C::Q, C::MR) + t;
                                 ysub[0] = cadd(a0, a2);
-                                ysub[C::SROW] = cmul(make_float2(a1.x + a3.y, a1.y - a3.x), tw4[0]);
-                                ysub[2 * C::SROW] = cmul(csub(a0, a2), tw4[C::Q]);
-                                ysub[3 * C::SROW] = cmul(make_float2(a1.x - a3.y, a1.y + a3.x), tw4[2 * C::Q]);
+                                // the twiddles w_P^(t k1) are applied by the FFT warps' first pass
+                                ysub[C::SROW] = make_float2(a1.x + a3.y, a1.y - a3.x);
+                                ysub[2 * C::SROW] = csub(a0, a2);
+                                ysub[3 * C::SROW] = make_float2(a1.x - a3.y, a1.y + a3.x);
                             } else {
                                 float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW;
 #pragma unroll
@@ -440,7 +455,8 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                 float2 *Yb = Y + (bc & 1) * (SB * YROW);
                 if constexpr (C::DIF4) {
                     Yb = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF);
-                    ws_pass<C::Q, C::MR, 4 * SB, 0, false, C::SROW, G>(Yb, W, tw, nullptr, 0, ft, C::NFFTT);
+                    ws_pass<C::Q, C::MR, 4 * SB, 0, false, C::SROW, G, true>(
+                        Yb, W, tw, nullptr, 0, ft, C::NFFTT, tw + fft_tw_entries(C::Q, C::MR));
                     named_bar_sync<1>(C::NFFTT);
                     if (ft == 0) mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
                     ws_dif4_last<C::Q, SB, C::SROW, G>(W, tw, mt.out, mt.nrows, ft, C::NFFTT);
