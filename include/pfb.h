@@ -128,9 +128,12 @@ PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samp
                        void *d_out, int64_t out_cap_spectra, void *cuda_stream);
 
 /* Same as pfb_execute, from and to HOST memory: the library stages the input
- * through device buffers it owns (host->device copy, kernel, device->host
- * copy) on cuda_stream and returns after the output is in host_out.  Pinned
- * host memory gives the fastest copies. */
+ * through device buffers it owns and returns after the output is in host_out.
+ * The work is pipelined over chunks of about 16 MB of input: host->device
+ * copies on an internal stream, kernels on cuda_stream, device->host copies
+ * on a second internal stream, so both copy directions and the kernels
+ * overlap; it starts after the work already queued on cuda_stream.  Results
+ * equal those of pfb_execute.  Pinned host memory gives the fastest copies. */
 PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples,
                             void *host_out, int64_t out_cap_spectra, void *cuda_stream);
 

@@ -79,6 +79,8 @@ enum KernelFamily : int {
     FAM_FFT_CLUSTER = 4,  // fused FIR + four-step FFT across a CTA cluster, P in {2048, 4096}
 };
 
+constexpr int kPipeChunks = 32;  // most chunks of one pfb_execute_host pipeline
+
 struct Plan {
     pfb_plan_desc desc;
     int device = 0;
@@ -102,6 +104,9 @@ struct Plan {
     std::mutex stage_mu;
     void *d_stage_in = nullptr, *d_stage_out = nullptr;
     size_t stage_in_bytes = 0, stage_out_bytes = 0;
+    // host-buffer pipeline: copy-in and copy-out streams, per-chunk events
+    cudaStream_t s_copy_in = nullptr, s_copy_out = nullptr;
+    cudaEvent_t ev_pipe[2 * kPipeChunks + 2] = {};
     std::string kernel_name;
 };
 

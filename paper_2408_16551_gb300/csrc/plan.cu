@@ -154,6 +154,10 @@ static void free_plan(Plan *p) {
     cudaFree(p->d_tw32);
     cudaFree(p->d_dft);
     cudaFree(p->d_err);
+    if (p->s_copy_in) cudaStreamDestroy(p->s_copy_in);
+    if (p->s_copy_out) cudaStreamDestroy(p->s_copy_out);
+    for (cudaEvent_t e : p->ev_pipe)
+        if (e) cudaEventDestroy(e);
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
     if (prev >= 0) cudaSetDevice(prev);

@@ -203,6 +203,25 @@ def test_execute_host_matches_device():
     assert np.array_equal(dev, host)
 
 
+@pytest.mark.parametrize("P,T,dt,n", [(1024, 16, synth.IN_C64, (5 << 22) + 3 * 1024 + 5),
+                                      (256, 8, synth.IN_CI8, (9 << 23) + 77),
+                                      (4096, 16, synth.IN_R32, (3 << 22) + 4096 * 7 + 1)])
+def test_execute_host_chunked_matches_device(P, T, dt, n):
+    """Host-buffer path over several pipeline chunks (input > 16 MB), ragged tail:
+    identical to the device-resident launch."""
+    import torch
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=12).generate()
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_HAMMING)
+    dev = plan.execute(to_device(x)).cpu().numpy()
+    host = plan.execute_host(x)
+    assert host.shape == dev.shape == (n // P - T + 1, P)
+    assert np.array_equal(dev, host)
+    xp = torch.from_numpy(x).pin_memory()
+    outp = torch.empty((n // P - T + 1, P), dtype=torch.complex64).pin_memory()
+    plan.execute_host(xp.numpy(), outp.numpy())
+    assert np.array_equal(dev, outp.numpy())
+
+
 @pytest.mark.parametrize("P,T,dt", [(1024, 16, synth.IN_C64), (512, 8, synth.IN_CI8), (256, 16, synth.IN_R32),
                                     (128, 4, synth.IN_C64), (64, 12, synth.IN_C64), (1024, 8, synth.IN_CI8),
                                     (1024, 4, synth.IN_R32), (512, 16, synth.IN_C64), (1024, 12, synth.IN_C64)])
