@@ -37,6 +37,7 @@
 #include "fftplan.h"
 #include "internal.h"
 #include "sync.cuh"
+#include "tc.cuh"
 
 namespace pfb {
 
@@ -44,7 +45,7 @@ namespace pfb {
 #define PFB_WS_DIF4 1
 #endif
 
-template <int P, int TT, int IN>
+template <int P, int TT, int IN, bool TC = false>
 struct WsCfg {
     static constexpr int NB = P >= 1024 ? 4 : (P >= 512 ? 2 : 1);  // branches per FIR thread
     static constexpr int NPAIR = NB >= 2 ? NB / 2 : 1;              // branch pairs (2t, 2t+1) + k P/NPAIR
@@ -52,7 +53,7 @@ struct WsCfg {
     // decimation-in-frequency butterfly before handing over; the FFT warps
     // apply its twiddles in their first pass and run four P/4-point
     // transforms per spectrum
-    static constexpr bool DIF4 = PFB_WS_DIF4 && (P == 1024);
+    static constexpr bool DIF4 = PFB_WS_DIF4 && (P == 1024) && !TC;
     static constexpr int Q = P / 4;                                  // sub-transform length (DIF4)
     static constexpr int SROW = Q + Q / 16 + 8;                      // sub-row stride (float2), 16 banks apart
     static constexpr int NFT = P / NB;                               // FIR threads
@@ -79,11 +80,24 @@ struct WsCfg {
     static constexpr int OFF_Y = OFF_RING + NSLOT * FB;
     static constexpr int YBUF = DIF4 ? SB * 4 * SROW * 8 : SB * YROW * 8;
     static constexpr int OFF_W = OFF_Y + 2 * YBUF;
-    static constexpr int OFF_TW = OFF_W + (DIF4 ? 1 : 2) * YBUF;
-    static constexpr int OFF_META = OFF_TW + (NTW > 0 ? NTW : 1) * 8;
+    static constexpr int OFF_TW = OFF_W + (TC ? 0 : (DIF4 ? 1 : 2) * YBUF);
+    // TC (tensor-core four-step DFT, P = 32 x 32): the step-2 A operand
+    // (bf16 hi and lo, K-major, 128 rows x 64), the 32-point DFT matrix in
+    // real block form (bf16 hi and lo, K-major tile of 64 x 64) and the
+    // twiddles w_P^(k1 n2) as a [k1][n2] table
+    static constexpr int TC_P1 = 32;
+    static constexpr int TC_LBO_A = 2064;                            // K-group stride: 16 B off 128 -> 4 banks
+    static constexpr int TC_A2B = 8 * TC_LBO_A;                      // bytes of one A2 term
+    static constexpr int TC_BTB = 64 * 64 * 2;                       // bytes of one B term
+    static constexpr int OFF_A2 = OFF_TW;
+    static constexpr int OFF_BT = OFF_A2 + (TC ? 2 * TC_A2B : 0);
+    static constexpr int OFF_TWT = OFF_BT + (TC ? 2 * TC_BTB : 0);
+    static constexpr int OFF_META = TC ? OFF_TWT + TC_P1 * TC_P1 * 8 : OFF_TW + (NTW > 0 ? NTW : 1) * 8;
     static constexpr int OFF_BAR = OFF_META + 3 * 32;
-    static constexpr int NBAR = 2 * NSLOT + 4;
+    static constexpr int NBAR = 2 * NSLOT + 4 + (TC ? 1 : 0);
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
+    static_assert(!TC || (P == TC_P1 * TC_P1 && SB * TC_P1 == 128), "TC: P = 32 x 32, 4 spectra per 128-row tile");
+    static_assert(!TC || (OFF_A2 % 128 == 0 && OFF_BT % 128 == 0), "TC operand alignment");
     static_assert(NFT % 128 == 0 || !SETMAXNREG, "FIR warps form whole warpgroups");
     static_assert(!DIF4 || (NB == 4 && NFT == Q && fft_npasses(Q, MR) == 2), "DIF4 layout");
     static_assert(NFIRW * 32 + NFFTT + (SETMAXNREG ? 128 : 32) == NTHREADS, "layout");
@@ -212,6 +226,19 @@ __device__ __forceinline__ void ws_dif4_last(const float2 *src, const float2 *tw
     }
 }
 
+// named barrier that also ORs a predicate over the participating threads
+template <int ID>
+__device__ __forceinline__ bool named_bar_or(int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(ID), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 // iterate the CTA's spectra range as (stream, [sA, sB)) segments
 struct WsRange {
     int64_t u, u1;
@@ -228,9 +255,157 @@ __device__ __forceinline__ bool ws_next_segment(const LaunchArgs &a, WsRange &r,
     return true;
 }
 
-template <int P, int TT, int IN>
-__global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const __grid_constant__ LaunchArgs a) {
-    using C = WsCfg<P, TT, IN>;
+// ---------------------------------------------------------------------------
+// Tensor-core DFT warps (TC): the DFT of Sec. 4.1 as two 32-point DFT-matrix
+// products on the tensor cores (four-step form, P = 32 x 32, p = 32 n1 + n2,
+// k = k1 + 32 k2), split-bf16 operands (hi = RN(v), lo = RN(v - hi); three
+// products hi*hi + hi*lo + lo*hi), FP32 accumulation in TMEM:
+//   Z[n2][k1]       = sum_{n1} y[32 n1 + n2] w_32^(n1 k1)        (MMA 1)
+//   X[k1 + 32 k2]   = sum_{n2} (Z[n2][k1] w_P^(n2 k1)) w_32^(n2 k2)  (MMA 2)
+// One batch = 4 spectra = one 128-row tile; warp w (TMEM lane quarter w mod 4)
+// owns spectrum w mod 4 of the batch.  MMA 1: A = branch sums in TMEM (row
+// (s, n2), K = (n1, re/im)), written by tcgen05.st; MMA 2: A in shared memory
+// (row (s, k1), K = (n2, re/im)), written transposed from the MMA 1 result
+// after the twiddle; B = the real block form [[Re, Im], [-Im, Re]] of the
+// 32-point DFT matrix, the same for both.  Bins leave straight from TMEM.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kTcCols = 256;                  // A1 [0, 64), D1 [64, 128), D2 [128, 192)
+constexpr uint32_t kTcColA1 = 0, kTcColD1 = 64, kTcColD2 = 128;
+
+template <class C>
+__device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, uint8_t *ws_smem, WsMeta *meta,
+                                          uint32_t yfull0, uint32_t yempty0, uint32_t mbar, uint32_t tmem,
+                                          volatile int *abort_flag, int ft, int warp, int lane) {
+    constexpr int SB = C::SB, YROW = C::YROW, G = C::G, P = C::TC_P1 * C::TC_P1, NT = C::NFFTT;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, 64);
+    constexpr int LBO_A = C::TC_LBO_A;
+    const int q = warp & 3;  // spectrum of the batch = TMEM lane quarter
+    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+    uint8_t *a2 = ws_smem + C::OFF_A2;
+    const uint32_t sA2 = smem_u32(a2), sBT = smem_u32(ws_smem + C::OFF_BT);
+    const float2 *twt = reinterpret_cast<const float2 *>(ws_smem + C::OFF_TWT);
+    const float2 *Y = reinterpret_cast<const float2 *>(ws_smem + C::OFF_Y);
+    uint32_t bc = 0, mph = 0;
+    bool ok = true;
+    int si;
+    int64_t sA, sB;
+    auto issue = [&](bool step2) {
+        tc_fence_after();
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {  // K = 64 in steps of 16
+            const uint64_t bh = tc_desc_kmajor(sBT + ks * 256, 128, 1024);
+            const uint64_t bl = tc_desc_kmajor(sBT + C::TC_BTB + ks * 256, 128, 1024);
+            if (!step2) {
+                const uint32_t d = tmem + kTcColD1, ah = tmem + kTcColA1 + 8 * ks, al = ah + 32;
+                tc_mma_ts(d, ah, bh, IDESC, ks > 0);
+                tc_mma_ts(d, ah, bl, IDESC, 1u);
+                tc_mma_ts(d, al, bh, IDESC, 1u);
+            } else {
+                const uint32_t d = tmem + kTcColD2;
+                const uint64_t ah = tc_desc_kmajor(sA2 + ks * 2 * LBO_A, LBO_A, 128);
+                const uint64_t al = tc_desc_kmajor(sA2 + C::TC_A2B + ks * 2 * LBO_A, LBO_A, 128);
+                tc_mma_ss(d, ah, bh, IDESC, ks > 0);
+                tc_mma_ss(d, ah, bl, IDESC, 1u);
+                tc_mma_ss(d, al, bh, IDESC, 1u);
+            }
+        }
+        tc_commit(mbar);
+    };
+    bool pending = false;  // an MMA commit not yet observed
+    while (ok && ws_next_segment(a, range, si, sA, sB)) {
+        const int64_t nb = (sB - sA + SB - 1) / SB;
+        for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
+            if (ft == 0) meta[2].nrows = mbar_wait(yfull0 + 8 * (bc & 1), (bc >> 1) & 1) ? 1 : 0;
+            named_bar_sync<1>(NT);
+            if (!meta[2].nrows) {
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            const WsMeta mt = meta[bc & 1];
+            // ---- MMA 1 operand: row (q, n2 = lane), K = (n1, re/im) ----
+            const float2 *yrow = Y + (bc & 1) * (SB * YROW) + q * YROW;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t vh[16], vl[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) split_bf16x2(yrow[ypad<G>(32 * (16 * h + j) + lane)], vh[j], vl[j]);
+                tmem_st<16>(trow + kTcColA1 + 16 * h, vh);
+                tmem_st<16>(trow + kTcColA1 + 32 + 16 * h, vl);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            named_bar_sync<1>(NT);
+            if (ft == 0) {
+                mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
+                issue(false);
+            }
+            pending = true;
+            bool w = mbar_wait(mbar, mph & 1);
+            ++mph;
+            if (named_bar_or<2>(NT, !w)) {
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            pending = false;
+            tc_fence_after();
+            // ---- twiddle, split, transposed store: MMA 2 operand row (q, k1), K = (n2 = lane, re/im) ----
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[32];
+                tmem_ld32(trow + kTcColD1 + 32 * h, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int k1 = 16 * h + j;
+                    const float2 z = cmul(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])),
+                                          twt[k1 * C::TC_P1 + lane]);
+                    uint32_t hi, lo;
+                    split_bf16x2(z, hi, lo);
+                    const int m = 32 * q + k1;
+                    const int off = (lane >> 2) * LBO_A + (m >> 3) * 128 + (m & 7) * 16 + (lane & 3) * 4;
+                    *reinterpret_cast<uint32_t *>(a2 + off) = hi;
+                    *reinterpret_cast<uint32_t *>(a2 + C::TC_A2B + off) = lo;
+                }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            named_bar_sync<1>(NT);
+            if (ft == 0) issue(true);
+            pending = true;
+            w = mbar_wait(mbar, mph & 1);
+            ++mph;
+            if (named_bar_or<2>(NT, !w)) {
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            pending = false;
+            tc_fence_after();
+            // ---- bins k1 + 32 k2 of spectrum q (thread k1 = lane) ----
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[32];
+                tmem_ld32(trow + kTcColD2 + 32 * h, r);
+                tmem_wait_ld();
+                if (q < mt.nrows) {
+                    float2 *o = mt.out + q * P + lane + 32 * (16 * h);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        store_cs(o + 32 * j, make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
+                }
+            }
+            tc_fence_before();
+        }
+    }
+    // a commit whose wait timed out: let it land before TMEM is freed
+    if (pending && ft == 0) mbar_wait(mbar, (mph - 1) & 1);
+}
+
+template <int P, int TT, int IN, bool TC = false>
+__global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(const __grid_constant__ LaunchArgs a) {
+    using C = WsCfg<P, TT, IN, TC>;
     constexpr int NB = C::NB, SB = C::SB, NSLOT = C::NSLOT, YROW = C::YROW, G = C::G;
     extern __shared__ __align__(128) uint8_t ws_smem[];
     uint8_t *ring = ws_smem + C::OFF_RING;
@@ -253,6 +428,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
             mbar_init(yfull0 + 8 * i, C::NFIRW);
             mbar_init(yempty0 + 8 * i, 1);
         }
+        if constexpr (TC) mbar_init(smem_u32(&bars[2 * NSLOT + 4]), 1);  // MMA completion
         mbar_init_fence();
         *abort_flag = 0;
     }
@@ -266,10 +442,23 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
             const float2 w = tw_half[r % (P / 2)];
             tw[NTQ + i] = r < P / 2 ? w : make_float2(-w.x, -w.y);
         }
+    } else if constexpr (TC) {
+        // DFT matrix hi/lo tiles and twiddles, 16-byte vectors
+        const int4 *src = static_cast<const int4 *>(a.aux);
+        int4 *dst = reinterpret_cast<int4 *>(ws_smem + C::OFF_BT);
+        constexpr int NV = (2 * C::TC_BTB + C::TC_P1 * C::TC_P1 * 8) / 16;
+        for (int i = threadIdx.x; i < NV; i += C::NTHREADS) dst[i] = src[i];
     } else {
         for (int i = threadIdx.x; i < C::NTW; i += C::NTHREADS) tw[i] = a.tw[i];
     }
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(abort_flag + 1);
+    if constexpr (TC) {
+        if (warp == C::NFIRW) tmem_alloc(smem_u32((const void *)tmem_slot), kTcCols);
+        fence_proxy_async_smem();  // the tables are read by the tensor core
+        tc_fence_before();
+    }
     __syncthreads();
+    if constexpr (TC) tc_fence_after();
 
     WsRange range;
     range.u = (int64_t)blockIdx.x * a.units_per_cta;
@@ -435,6 +624,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
         // ======================= FFT warps =======================
         if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
         const int ft = threadIdx.x - C::NFT;
+        if constexpr (TC) {
+            ws_tc_dft<C>(a, range, ws_smem, meta, yfull0, yempty0, smem_u32(&bars[2 * NSLOT + 4]), *tmem_slot,
+                         abort_flag, ft, warp, lane);
+        } else {
         uint32_t bc = 0;
         bool ok = true;
         int si;
@@ -466,6 +659,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
                 }
                 named_bar_sync<1>(C::NFFTT);  // W buffers free before the next batch
             }
+        }
         }
     } else {
         // ======================= producer warp(group) =======================
@@ -501,15 +695,22 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN>::NTHREADS, 1) k_fft_ws(const 
         }
         __syncwarp();
     }
+    if constexpr (TC) tc_fence_before();
     __syncthreads();
+    if constexpr (TC) {
+        if (warp == C::NFIRW) {
+            tc_fence_after();
+            tmem_dealloc(*tmem_slot, kTcCols);
+        }
+    }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
 }
 
 // rows of the launch: one work unit per spectrum
-template <int P, int TT, int IN>
+template <int P, int TT, int IN, bool TC = false>
 static pfb_status launch_fft_ws_k(LaunchArgs &a, cudaStream_t stream) {
-    using C = WsCfg<P, TT, IN>;
-    auto k = k_fft_ws<P, TT, IN>;
+    using C = WsCfg<P, TT, IN, TC>;
+    auto k = k_fft_ws<P, TT, IN, TC>;
     static int grid_cap = 0;
     if (grid_cap == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);

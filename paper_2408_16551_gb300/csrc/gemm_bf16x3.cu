@@ -38,6 +38,7 @@
 #include "devutil.cuh"
 #include "internal.h"
 #include "sync.cuh"
+#include "tc.cuh"
 
 namespace pfb {
 
@@ -55,10 +56,11 @@ constexpr uint32_t K2_COL_A = 256;                 // A stages start after the 2
 constexpr int K2_CHUNK = 8;                        // K blocks per TMEM accumulation chunk
 
 // instruction descriptor, kind::f16: D=f32, A=B=bf16, K-major A and B, N=256, M=128
-constexpr uint32_t K2_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(K2_N >> 3) << 17) |
-                              ((uint32_t)(K2_M >> 4) << 24);
+constexpr uint32_t K2_IDESC = tc_idesc_bf16(K2_M, K2_N);
 
+// variant 0: (128-spectrum M tile, 128-bin N tile) pairs; variant 1 (factored): spectra
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) {
+    if (plan.variant == 1) return S;
     return ((S + K2_M - 1) / K2_M) * (plan.P / (K2_N / 2));
 }
 
@@ -111,6 +113,10 @@ pfb_status build_gemm_tables(Plan &plan) {
     if (plan.family == FAM_GEMM_F32) return build_gemm_f32_table(plan);
     if (plan.family == FAM_GEMM_BF16X3) {
         if (plan.P < K2_N / 2 || plan.T > 16) return PFB_OK;  // no kernel; execute reports UNSUPPORTED
+        if (tcf_supported(plan)) {
+            pfb_status st = build_tcf_table(plan);
+            if (st != PFB_OK) return st;
+        }
         return build_gemm_bf16x3_table(plan);
     }
     return PFB_OK;
@@ -120,63 +126,15 @@ pfb_status build_gemm_tables(Plan &plan) {
 // PTX helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    // start address, LBO = 128 B (K direction), SBO = 1024 B (N direction),
-    // version 1 (bit 46), no swizzle
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           (1ull << 46);
+    // B tiles: LBO = 128 B (K direction), SBO = 1024 B (N direction)
+    return tc_desc_kmajor(addr, 128, 1024);
 }
 
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %4, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(accumulate), "r"(K2_IDESC)
-        : "memory");
+    tc_mma_ts(d_tmem, a_tmem, b_desc, K2_IDESC, accumulate);
 }
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(K2_THREADS) : "memory"); }
-
-template <int N>
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[N]);
-
-template <>
-__device__ __forceinline__ void tmem_st32<32>(uint32_t taddr, const uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-        : "memory");
-}
-
-template <>
-__device__ __forceinline__ void tmem_st32<16>(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
 
 // Move 128 columns (this warp's half) of this thread's accumulator row into
 // the output tile row: first chunk stores, later chunks add (FP32, RN).
@@ -344,8 +302,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                     __syncwarp();
                     const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
                     const uint32_t acol = K2_COL_A + 64 * stage + 16 * hb;
-                    tmem_st32<16>(trow + acol, vh);
-                    tmem_st32<16>(trow + acol + 32, vl);
+                    tmem_st<16>(trow + acol, vh);
+                    tmem_st<16>(trow + acol + 32, vl);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     if (kb > 0 && kb % K2_CHUNK == 0) {
                         // chunk boundary: the previous K block's MMAs end the chunk; move the
@@ -465,6 +423,7 @@ static pfb_status launch_k2_t(const Plan &plan, LaunchArgs &a, cudaStream_t stre
 }
 
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    if (plan.variant == 1) return launch_gemm_bf16x3_tcf(plan, a, stream);
     if (plan.P < K2_N / 2) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs P >= 128");
     if (plan.T > 16) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs T <= 16");
     switch (plan.in_dtype) {

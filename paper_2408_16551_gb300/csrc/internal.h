@@ -98,6 +98,7 @@ struct Plan {
     float2 *d_tw32 = nullptr;       // radix-32 pass list twiddles (fast FFT family)
     float2 *d_tw_r2 = nullptr;      // radix-2 table w^r, r < P/2 (generic family)
     void *d_dft = nullptr;          // DFT matrix (GEMM families)
+    void *d_tcf = nullptr;          // factored split-bf16 DFT: 32-point matrix hi/lo + twiddles
     size_t dft_bytes = 0;
     int *d_err = nullptr;           // device error word
     // host staging for pfb_execute_host
@@ -123,6 +124,9 @@ pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &args, cudaStream_t stre
 pfb_status launch_fft_generic(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status launch_gemm_bf16x3_tcf(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+bool tcf_supported(const Plan &plan);
+pfb_status build_tcf_table(Plan &plan);
 pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 bool fft_cluster_supported(int P, int T);
 pfb_status prepare_family(const Plan &plan);

@@ -153,6 +153,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->d_tw_r2);
     cudaFree(p->d_tw32);
     cudaFree(p->d_dft);
+    cudaFree(p->d_tcf);
     cudaFree(p->d_err);
     if (p->s_copy_in) cudaStreamDestroy(p->s_copy_in);
     if (p->s_copy_out) cudaStreamDestroy(p->s_copy_out);

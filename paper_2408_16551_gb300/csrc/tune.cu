@@ -75,16 +75,25 @@ static void save_file_cache() {
     std::rename((std::string(path) + ".tmp").c_str(), path);
 }
 
-int family_variants(const Plan &plan) { return plan.family == FAM_FFT_FAST ? 6 : 1; }
+// fast FFT family: 6 tile shapes; split-bf16 family: 0 = dense DFT-matrix
+// product, 1 = factored (four-step) tensor-core DFT
+int family_variants(const Plan &plan) {
+    if (plan.family == FAM_FFT_FAST) return 6;
+    if (plan.family == FAM_GEMM_BF16X3) return 2;
+    return 1;
+}
 
-// variant 5 of the fast FFT family needs P >= 128 and T equal to its tap count
+// variant 5 of the fast FFT family needs P >= 128 and T equal to its tap count;
+// the factored split-bf16 DFT needs P = 1024 and T equal to its tap count
 static bool variant_supported(const Plan &plan, int v) {
     if (plan.family == FAM_FFT_FAST && v == 5) return plan.P >= 128 && plan.T == plan.TT;
+    if (plan.family == FAM_GEMM_BF16X3 && v == 1) return tcf_supported(plan);
     return v >= 0 && v < family_variants(plan);
 }
 
 int default_variant(const Plan &plan) {
     if (family_variants(plan) <= 1) return 0;
+    if (plan.family == FAM_GEMM_BF16X3) return tcf_supported(plan) ? 1 : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_file_cache();
     auto it = g_tune_cache.find(key_of(plan));

@@ -57,12 +57,23 @@ def test_gemm_bf16x3_parity(P, T, dt):
     assert e2 > 1e-8          # split arithmetic is not exact: the kernel really ran the bf16 path
 
 
+def _run_variant(variant, P, T, dt, n, seed=0, window=synth.WIN_HANN):
+    import torch
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=seed, window=window).generate()
+    plan = pkg.Plan(P, T, dt, window, pkg.PFB_DFT_GEMM_BF16X3)
+    plan.variant = variant
+    X = plan.execute(to_device(x))
+    torch.cuda.synchronize()
+    return plan, x, X.cpu().numpy()
+
+
 @pytest.mark.parametrize("P,T", [(256, 8), (1024, 16)])
 def test_gemm_bf16x3_matches_split_model(P, T):
-    """Against the FP64 model of the split arithmetic (hi*hi + hi*lo + lo*hi):
-    agreement to FP32-accumulation error separates split error from indexing."""
+    """Dense DFT-matrix product (variant 0) against the FP64 model of the split
+    arithmetic (hi*hi + hi*lo + lo*hi): agreement to FP32-accumulation error
+    separates split error from indexing."""
     n = P * (T - 1 + 200)
-    plan, x, got = _run(pkg.PFB_DFT_GEMM_BF16X3, P, T, synth.IN_C64, n, seed=9)
+    plan, x, got = _run_variant(0, P, T, synth.IN_C64, n, seed=9)
     h = oracle.prototype(P, T, oracle.WIN_HANN)
     y = oracle.fir(oracle.dequant(x, oracle.IN_C64), P, T, h)
     model = oracle.split_bf16x3_model(y.astype(np.complex64), P)
@@ -112,3 +123,75 @@ def test_gemm_paths_report_unsupported_shapes():
     with pytest.raises(pkg.PFBError) as ei:
         plan.execute(torch.zeros(256 * 40, dtype=torch.complex64, device="cuda"))
     assert ei.value.status == pkg.PFB_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# factored (four-step) tensor-core DFT, variant 1 (P = 32 x 32)
+# ---------------------------------------------------------------------------
+
+def test_factored_is_the_default_at_p1024():
+    plan = pkg.Plan(1024, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan.num_variants == 2 and plan.variant == 1
+    plan2 = pkg.Plan(1024, 12, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan2.variant == 0                 # T = 12 is not a compiled tap count
+    with pytest.raises(pkg.PFBError):
+        plan2.variant = 1
+    plan3 = pkg.Plan(512, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan3.variant == 0
+
+
+@pytest.mark.parametrize("T,dt,rows", [(16, synth.IN_C64, 4 * 37 + 3), (8, synth.IN_CI8, 4 * 20 + 1),
+                                       (4, synth.IN_R32, 4 * 9 + 2), (16, synth.IN_C64, 2),
+                                       (16, synth.IN_R32, 4 * 160)])
+def test_gemm_bf16x3_factored_parity(T, dt, rows):
+    """Several 4-spectrum tiles with ragged last tiles (and a stream shorter than
+    one tile) against the FP64 oracle at the split-bf16 bound."""
+    P = 1024
+    n = P * (T - 1 + rows) + 7
+    plan, x, got = _run_variant(1, P, T, dt, n, seed=T * 7 + rows)
+    ref = reference(x, dt, P, T, synth.WIN_HANN)
+    assert got.shape == ref.shape == (rows, P)
+    e2, em = assert_close(got, ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"bf16x3 factored T={T} rows={rows}")
+    assert e2 > 1e-8
+
+
+def test_gemm_bf16x3_factored_matches_model():
+    """Against the FP64 model of the four-step split arithmetic: a wrong tile,
+    transpose or twiddle index shows up as an O(1) error here."""
+    P, T = 1024, 16
+    n = P * (T - 1 + 96)
+    plan, x, got = _run_variant(1, P, T, synth.IN_C64, n, seed=19)
+    h = oracle.prototype(P, T, oracle.WIN_HANN)
+    y = oracle.fir(oracle.dequant(x, oracle.IN_C64), P, T, h)
+    model = oracle.factored_dft_model(y.astype(np.complex64), 32, 32)
+    e_model = oracle.rel_l2(got, model)
+    e_exact = oracle.rel_l2(got, oracle.dft(y))
+    assert e_model < 2e-6, e_model
+    assert e_exact < 1e-5, e_exact
+
+
+def test_gemm_bf16x3_factored_batch_and_c2_sample():
+    """Uneven streams in one batched launch equal their single launches; the
+    full c2 workload on the factored path, sampled rows against the oracle."""
+    import torch
+    P, T = 1024, 16
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, synth.WIN_HAMMING, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan.variant == 1
+    xs = [to_device(synth.small_stream(P, T, P * (T - 1 + r) + 5, seed=r).generate()) for r in (1, 7, 64, 130)]
+    singles = [plan.execute(x).clone() for x in xs]
+    outs = [torch.empty_like(o) for o in singles]
+    pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xs, outs)])
+    torch.cuda.synchronize()
+    for a, b in zip(outs, singles):
+        assert torch.equal(a, b)
+    spec = synth.config_c2()
+    x = spec.generate()
+    X = plan.execute(to_device(x))
+    torch.cuda.synchronize()
+    S = X.shape[0]
+    rows = [0, 1, 2, 3, S // 2, S - 2, S - 1]
+    h = oracle.prototype(P, T, oracle.WIN_HAMMING)
+    got = X[rows].cpu().numpy()
+    xin = oracle.dequant(x, oracle.IN_C64)
+    ref = np.stack([oracle.dft(oracle.fir(xin, P, T, h, s0=r, ns=1))[0] for r in rows])
+    assert oracle.rel_l2(got, ref) < TOL_BF16X3

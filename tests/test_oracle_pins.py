@@ -347,3 +347,23 @@ def test_split_model_error_is_small_but_nonzero():
     ref = np.fft.fft(y.astype(np.complex128), axis=1)
     e = oracle.rel_l2(X, ref)
     assert 1e-7 < e < 1e-5
+
+
+@pytest.mark.parametrize("P1,P2", [(4, 4), (2, 8), (8, 2), (32, 32), (16, 4)])
+def test_factored_dft_model_unsplit_is_the_dft(P1, P2):
+    """Four-step factoring (p = P2 n1 + n2, k = k1 + P1 k2, twiddle w_P^(n2 k1))
+    against numpy.fft: a wrong index role, twiddle sign or output order fails."""
+    rng = np.random.default_rng(P1 * 100 + P2)
+    y = rng.standard_normal((6, P1 * P2)) + 1j * rng.standard_normal((6, P1 * P2))
+    ref = np.fft.fft(y, axis=1)
+    got = oracle.factored_dft_model(y, P1, P2, split=False)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_factored_dft_model_split_error_is_bounded():
+    """Split-bf16 four-step model at P = 32 x 32: error at the split level (two
+    products of hi/lo operands), inside the 1e-5 bound, and not zero."""
+    rng = np.random.default_rng(31)
+    y = (rng.standard_normal((6, 1024)) + 1j * rng.standard_normal((6, 1024))).astype(np.complex64)
+    e = oracle.rel_l2(oracle.factored_dft_model(y, 32, 32), np.fft.fft(y.astype(np.complex128), axis=1))
+    assert 1e-7 < e < 1e-5
