@@ -94,7 +94,7 @@ struct WsCfg {
     static constexpr int OFF_TWT = OFF_BT + (TC ? 2 * TC_BTB : 0);
     static constexpr int OFF_META = TC ? OFF_TWT + TC_P1 * TC_P1 * 8 : OFF_TW + (NTW > 0 ? NTW : 1) * 8;
     static constexpr int OFF_BAR = OFF_META + 3 * 32;
-    static constexpr int NBAR = 2 * NSLOT + 4 + (TC ? 1 : 0);
+    static constexpr int NBAR = 2 * NSLOT + 4 + (TC ? 2 : 0);
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
     static_assert(!TC || (P == TC_P1 * TC_P1 && SB * TC_P1 == 128), "TC: P = 32 x 32, 4 spectra per 128-row tile");
     static_assert(!TC || (OFF_A2 % 128 == 0 && OFF_BT % 128 == 0), "TC operand alignment");
@@ -274,8 +274,8 @@ constexpr uint32_t kTcColA1 = 0, kTcColD1 = 64, kTcColD2 = 128;
 
 template <class C>
 __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, uint8_t *ws_smem, WsMeta *meta,
-                                          uint32_t yfull0, uint32_t yempty0, uint32_t mbar, uint32_t tmem,
-                                          volatile int *abort_flag, int ft, int warp, int lane) {
+                                          uint32_t yfull0, uint32_t yempty0, uint32_t mbar1, uint32_t mbar2,
+                                          uint32_t tmem, volatile int *abort_flag, int ft, int warp, int lane) {
     constexpr int SB = C::SB, YROW = C::YROW, G = C::G, P = C::TC_P1 * C::TC_P1, NT = C::NFFTT;
     constexpr uint32_t IDESC = tc_idesc_bf16(128, 64);
     constexpr int LBO_A = C::TC_LBO_A;
@@ -285,11 +285,9 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
     const uint32_t sA2 = smem_u32(a2), sBT = smem_u32(ws_smem + C::OFF_BT);
     const float2 *twt = reinterpret_cast<const float2 *>(ws_smem + C::OFF_TWT);
     const float2 *Y = reinterpret_cast<const float2 *>(ws_smem + C::OFF_Y);
-    uint32_t bc = 0, mph = 0;
-    bool ok = true;
-    int si;
-    int64_t sA, sB;
-    auto issue = [&](bool step2) {
+    // a2 byte offset of this thread's (re, im) pair in row m = 32 q + k1, K = (n2 = lane, re/im)
+    const int a2_base = (lane >> 2) * LBO_A + (lane & 3) * 4 + (4 * q) * 128;
+    auto issue = [&](bool step2, uint32_t bar) {
         tc_fence_after();
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {  // K = 64 in steps of 16
@@ -309,9 +307,39 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
                 tc_mma_ss(d, al, bh, IDESC, 1u);
             }
         }
-        tc_commit(mbar);
+        tc_commit(bar);
     };
-    bool pending = false;  // an MMA commit not yet observed
+    // every DFT thread waits; the barrier ORs the failures so all take the same path
+    uint32_t ph1 = 0, ph2 = 0;  // completions observed on mbar1 / mbar2
+    uint32_t is1 = 0, is2 = 0;  // commits issued to mbar1 / mbar2 (thread ft == 0)
+    auto wait_mma = [&](uint32_t bar, uint32_t &ph) {
+        const bool w = mbar_wait(bar, ph & 1);
+        ++ph;
+        const bool fail = named_bar_or<2>(NT, !w);
+        tc_fence_after();
+        return !fail;
+    };
+    // bins k1 + 32 k2 of spectrum q of a finished batch (thread k1 = lane)
+    auto epilogue = [&](const WsMeta &mt) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(trow + kTcColD2 + 32 * h, r);
+            tmem_wait_ld();
+            if (q < mt.nrows) {
+                float2 *o = mt.out + q * P + lane + 32 * (16 * h);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    store_cs(o + 32 * j, make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
+            }
+        }
+    };
+    uint32_t bc = 0;
+    bool ok = true, have_prev = false;
+    WsMeta mt_prev;
+    int si;
+    int64_t sA, sB;
+    // Software pipeline over batches b: T1(b), MMA 1(b) | epilogue(b-1) ; T2(b), MMA 2(b) | T1(b+1) ...
     while (ok && ws_next_segment(a, range, si, sA, sB)) {
         const int64_t nb = (sB - sA + SB - 1) / SB;
         for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
@@ -323,7 +351,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
                 break;
             }
             const WsMeta mt = meta[bc & 1];
-            // ---- MMA 1 operand: row (q, n2 = lane), K = (n1, re/im) ----
+            // ---- MMA 1 operand: row (q, n2 = lane), K = (n1, re/im), into TMEM ----
             const float2 *yrow = Y + (bc & 1) * (SB * YROW) + q * YROW;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -338,18 +366,24 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
             named_bar_sync<1>(NT);
             if (ft == 0) {
                 mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
-                issue(false);
+                issue(false, mbar1);
+                ++is1;
             }
-            pending = true;
-            bool w = mbar_wait(mbar, mph & 1);
-            ++mph;
-            if (named_bar_or<2>(NT, !w)) {
+            // ---- while MMA 1 runs: the previous batch's bins ----
+            if (have_prev) {
+                if (!wait_mma(mbar2, ph2)) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                epilogue(mt_prev);
+                have_prev = false;
+            }
+            if (!wait_mma(mbar1, ph1)) {
                 *abort_flag = 1;
                 ok = false;
                 break;
             }
-            pending = false;
-            tc_fence_after();
             // ---- twiddle, split, transposed store: MMA 2 operand row (q, k1), K = (n2 = lane, re/im) ----
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -363,8 +397,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
                                           twt[k1 * C::TC_P1 + lane]);
                     uint32_t hi, lo;
                     split_bf16x2(z, hi, lo);
-                    const int m = 32 * q + k1;
-                    const int off = (lane >> 2) * LBO_A + (m >> 3) * 128 + (m & 7) * 16 + (lane & 3) * 4;
+                    const int off = a2_base + (k1 >> 3) * 128 + (k1 & 7) * 16;
                     *reinterpret_cast<uint32_t *>(a2 + off) = hi;
                     *reinterpret_cast<uint32_t *>(a2 + C::TC_A2B + off) = lo;
                 }
@@ -372,35 +405,23 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
             fence_proxy_async_smem();
             tc_fence_before();
             named_bar_sync<1>(NT);
-            if (ft == 0) issue(true);
-            pending = true;
-            w = mbar_wait(mbar, mph & 1);
-            ++mph;
-            if (named_bar_or<2>(NT, !w)) {
-                *abort_flag = 1;
-                ok = false;
-                break;
+            if (ft == 0) {
+                issue(true, mbar2);
+                ++is2;
             }
-            pending = false;
-            tc_fence_after();
-            // ---- bins k1 + 32 k2 of spectrum q (thread k1 = lane) ----
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t r[32];
-                tmem_ld32(trow + kTcColD2 + 32 * h, r);
-                tmem_wait_ld();
-                if (q < mt.nrows) {
-                    float2 *o = mt.out + q * P + lane + 32 * (16 * h);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        store_cs(o + 32 * j, make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
-                }
-            }
-            tc_fence_before();
+            mt_prev = mt;
+            have_prev = true;
         }
     }
-    // a commit whose wait timed out: let it land before TMEM is freed
-    if (pending && ft == 0) mbar_wait(mbar, (mph - 1) & 1);
+    if (ok && have_prev) {
+        if (wait_mma(mbar2, ph2)) epilogue(mt_prev);
+        else *abort_flag = 1;
+    }
+    // commits whose completion was not observed (abort): let them land before TMEM is freed
+    if (ft == 0) {
+        if (is1 > ph1) mbar_wait(mbar1, (is1 - 1) & 1);
+        if (is2 > ph2) mbar_wait(mbar2, (is2 - 1) & 1);
+    }
 }
 
 template <int P, int TT, int IN, bool TC = false>
@@ -428,7 +449,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
             mbar_init(yfull0 + 8 * i, C::NFIRW);
             mbar_init(yempty0 + 8 * i, 1);
         }
-        if constexpr (TC) mbar_init(smem_u32(&bars[2 * NSLOT + 4]), 1);  // MMA completion
+        if constexpr (TC) {  // MMA 1 / MMA 2 completion
+            mbar_init(smem_u32(&bars[2 * NSLOT + 4]), 1);
+            mbar_init(smem_u32(&bars[2 * NSLOT + 5]), 1);
+        }
         mbar_init_fence();
         *abort_flag = 0;
     }
@@ -625,7 +649,8 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
         const int ft = threadIdx.x - C::NFT;
         if constexpr (TC) {
-            ws_tc_dft<C>(a, range, ws_smem, meta, yfull0, yempty0, smem_u32(&bars[2 * NSLOT + 4]), *tmem_slot,
+            ws_tc_dft<C>(a, range, ws_smem, meta, yfull0, yempty0, smem_u32(&bars[2 * NSLOT + 4]),
+                         smem_u32(&bars[2 * NSLOT + 5]), *tmem_slot,
                          abort_flag, ft, warp, lane);
         } else {
         uint32_t bc = 0;
