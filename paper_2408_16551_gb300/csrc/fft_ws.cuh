@@ -94,10 +94,11 @@ struct WsCfg {
     static constexpr int OFF_TWT = OFF_BT + (TC ? 2 * TC_BTB : 0);
     static constexpr int OFF_META = TC ? OFF_TWT + TC_P1 * TC_P1 * 8 : OFF_TW + (NTW > 0 ? NTW : 1) * 8;
     static constexpr int OFF_BAR = OFF_META + 3 * 32;
-    static constexpr int NBAR = 2 * NSLOT + 4 + (TC ? 2 : 0);
+    static constexpr int NBAR = 2 * NSLOT + 4 + (TC ? 4 : 0);  // TC: MMA 1/2 done, operand 1/2 ready
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
     static_assert(!TC || (P == TC_P1 * TC_P1 && SB * TC_P1 == 128), "TC: P = 32 x 32, 4 spectra per 128-row tile");
     static_assert(!TC || (OFF_A2 % 128 == 0 && OFF_BT % 128 == 0), "TC operand alignment");
+    static_assert(!TC || SETMAXNREG, "TC: the MMA issuer is a warp of the producer warpgroup");
     static_assert(NFT % 128 == 0 || !SETMAXNREG, "FIR warps form whole warpgroups");
     static_assert(!DIF4 || (NB == 4 && NFT == Q && fft_npasses(Q, MR) == 2), "DIF4 layout");
     static_assert(NFIRW * 32 + NFFTT + (SETMAXNREG ? 128 : 32) == NTHREADS, "layout");
@@ -272,46 +273,87 @@ __device__ __forceinline__ bool ws_next_segment(const LaunchArgs &a, WsRange &r,
 constexpr uint32_t kTcCols = 256;                  // A1 [0, 64), D1 [64, 128), D2 [128, 192)
 constexpr uint32_t kTcColA1 = 0, kTcColD1 = 64, kTcColD2 = 128;
 
+// MMA issue for one batch: step 1 (A in TMEM) or step 2 (A in shared memory),
+// 4 K-steps x 3 split products, then a commit to `bar`
+template <class C>
+__device__ __forceinline__ void ws_tc_issue(bool step2, uint32_t tmem, uint32_t sA2, uint32_t sBT, uint32_t bar) {
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, 64);
+    constexpr int LBO_A = C::TC_LBO_A;
+#pragma unroll 1
+    for (int ks = 0; ks < 4; ++ks) {  // K = 64 in steps of 16
+        const uint64_t bh = tc_desc_kmajor(sBT + ks * 256, 128, 1024);
+        const uint64_t bl = tc_desc_kmajor(sBT + C::TC_BTB + ks * 256, 128, 1024);
+        if (!step2) {
+            const uint32_t d = tmem + kTcColD1, ah = tmem + kTcColA1 + 8 * ks, al = ah + 32;
+            tc_mma_ts(d, ah, bh, IDESC, ks > 0);
+            tc_mma_ts(d, ah, bl, IDESC, 1u);
+            tc_mma_ts(d, al, bh, IDESC, 1u);
+        } else {
+            const uint32_t d = tmem + kTcColD2;
+            const uint64_t ah = tc_desc_kmajor(sA2 + ks * 2 * LBO_A, LBO_A, 128);
+            const uint64_t al = tc_desc_kmajor(sA2 + C::TC_A2B + ks * 2 * LBO_A, LBO_A, 128);
+            tc_mma_ss(d, ah, bh, IDESC, ks > 0);
+            tc_mma_ss(d, ah, bl, IDESC, 1u);
+            tc_mma_ss(d, al, bh, IDESC, 1u);
+        }
+    }
+    tc_commit(bar);
+}
+
+// The MMA issuer (one thread of the producer warpgroup): per batch, waits for
+// the DFT warps' step-1 operand, issues MMA 1, waits for the step-2 operand,
+// issues MMA 2.  Keeps the tensor-core issue off the DFT warps' path.
+template <class C>
+__device__ __forceinline__ void ws_tc_mma_thread(const LaunchArgs &a, WsRange range, uint8_t *ws_smem, uint32_t op1,
+                                                 uint32_t op2, uint32_t mbar1, uint32_t mbar2, uint32_t tmem,
+                                                 volatile int *abort_flag) {
+    constexpr int SB = C::SB;
+    const uint32_t sA2 = smem_u32(ws_smem + C::OFF_A2), sBT = smem_u32(ws_smem + C::OFF_BT);
+    uint32_t bc = 0, issued1 = 0, issued2 = 0;
+    bool ok = true;
+    int si;
+    int64_t sA, sB;
+    while (ok && ws_next_segment(a, range, si, sA, sB)) {
+        const int64_t nb = (sB - sA + SB - 1) / SB;
+        for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
+            if (!mbar_wait(op1, bc & 1)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            ws_tc_issue<C>(false, tmem, sA2, sBT, mbar1);
+            ++issued1;
+            if (!mbar_wait(op2, bc & 1)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            ws_tc_issue<C>(true, tmem, sA2, sBT, mbar2);
+            ++issued2;
+        }
+    }
+    if (!ok) *abort_flag = 1;
+    // everything issued has completed before the CTA frees TMEM
+    if (issued1 && !mbar_wait(mbar1, (issued1 - 1) & 1)) *abort_flag = 1;
+    if (issued2 && !mbar_wait(mbar2, (issued2 - 1) & 1)) *abort_flag = 1;
+}
+
 template <class C>
 __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, uint8_t *ws_smem, WsMeta *meta,
-                                          uint32_t yfull0, uint32_t yempty0, uint32_t mbar1, uint32_t mbar2,
-                                          uint32_t tmem, volatile int *abort_flag, int ft, int warp, int lane) {
+                                          uint32_t yfull0, uint32_t yempty0, uint32_t op1, uint32_t op2,
+                                          uint32_t mbar1, uint32_t mbar2, uint32_t tmem, volatile int *abort_flag,
+                                          int ft, int warp, int lane) {
     constexpr int SB = C::SB, YROW = C::YROW, G = C::G, P = C::TC_P1 * C::TC_P1, NT = C::NFFTT;
-    constexpr uint32_t IDESC = tc_idesc_bf16(128, 64);
     constexpr int LBO_A = C::TC_LBO_A;
     const int q = warp & 3;  // spectrum of the batch = TMEM lane quarter
     const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
     uint8_t *a2 = ws_smem + C::OFF_A2;
-    const uint32_t sA2 = smem_u32(a2), sBT = smem_u32(ws_smem + C::OFF_BT);
     const float2 *twt = reinterpret_cast<const float2 *>(ws_smem + C::OFF_TWT);
     const float2 *Y = reinterpret_cast<const float2 *>(ws_smem + C::OFF_Y);
     // a2 byte offset of this thread's (re, im) pair in row m = 32 q + k1, K = (n2 = lane, re/im)
     const int a2_base = (lane >> 2) * LBO_A + (lane & 3) * 4 + (4 * q) * 128;
-    auto issue = [&](bool step2, uint32_t bar) {
-        tc_fence_after();
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {  // K = 64 in steps of 16
-            const uint64_t bh = tc_desc_kmajor(sBT + ks * 256, 128, 1024);
-            const uint64_t bl = tc_desc_kmajor(sBT + C::TC_BTB + ks * 256, 128, 1024);
-            if (!step2) {
-                const uint32_t d = tmem + kTcColD1, ah = tmem + kTcColA1 + 8 * ks, al = ah + 32;
-                tc_mma_ts(d, ah, bh, IDESC, ks > 0);
-                tc_mma_ts(d, ah, bl, IDESC, 1u);
-                tc_mma_ts(d, al, bh, IDESC, 1u);
-            } else {
-                const uint32_t d = tmem + kTcColD2;
-                const uint64_t ah = tc_desc_kmajor(sA2 + ks * 2 * LBO_A, LBO_A, 128);
-                const uint64_t al = tc_desc_kmajor(sA2 + C::TC_A2B + ks * 2 * LBO_A, LBO_A, 128);
-                tc_mma_ss(d, ah, bh, IDESC, ks > 0);
-                tc_mma_ss(d, ah, bl, IDESC, 1u);
-                tc_mma_ss(d, al, bh, IDESC, 1u);
-            }
-        }
-        tc_commit(bar);
-    };
     // every DFT thread waits; the barrier ORs the failures so all take the same path
     uint32_t ph1 = 0, ph2 = 0;  // completions observed on mbar1 / mbar2
-    uint32_t is1 = 0, is2 = 0;  // commits issued to mbar1 / mbar2 (thread ft == 0)
     auto wait_mma = [&](uint32_t bar, uint32_t &ph) {
         const bool w = mbar_wait(bar, ph & 1);
         ++ph;
@@ -339,7 +381,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
     WsMeta mt_prev;
     int si;
     int64_t sA, sB;
-    // Software pipeline over batches b: T1(b), MMA 1(b) | epilogue(b-1) ; T2(b), MMA 2(b) | T1(b+1) ...
+    // Pipeline over batches b: T1(b) | MMA 1(b) under epilogue(b-1) ; T2(b) | MMA 2(b) under T1(b+1)
     while (ok && ws_next_segment(a, range, si, sA, sB)) {
         const int64_t nb = (sB - sA + SB - 1) / SB;
         for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
@@ -362,13 +404,9 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
                 tmem_st<16>(trow + kTcColA1 + 32 + 16 * h, vl);
             }
             tmem_wait_st();
+            mbar_arrive(yempty0 + 8 * (bc & 1));  // this thread is done with Y
             tc_fence_before();
-            named_bar_sync<1>(NT);
-            if (ft == 0) {
-                mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
-                issue(false, mbar1);
-                ++is1;
-            }
+            mbar_arrive(op1);
             // ---- while MMA 1 runs: the previous batch's bins ----
             if (have_prev) {
                 if (!wait_mma(mbar2, ph2)) {
@@ -404,11 +442,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            named_bar_sync<1>(NT);
-            if (ft == 0) {
-                issue(true, mbar2);
-                ++is2;
-            }
+            mbar_arrive(op2);
             mt_prev = mt;
             have_prev = true;
         }
@@ -416,11 +450,6 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
     if (ok && have_prev) {
         if (wait_mma(mbar2, ph2)) epilogue(mt_prev);
         else *abort_flag = 1;
-    }
-    // commits whose completion was not observed (abort): let them land before TMEM is freed
-    if (ft == 0) {
-        if (is1 > ph1) mbar_wait(mbar1, (is1 - 1) & 1);
-        if (is2 > ph2) mbar_wait(mbar2, (is2 - 1) & 1);
     }
 }
 
@@ -447,11 +476,13 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(yfull0 + 8 * i, C::NFIRW);
-            mbar_init(yempty0 + 8 * i, 1);
+            mbar_init(yempty0 + 8 * i, TC ? C::NFFTT : 1);  // TC: every DFT thread releases Y
         }
-        if constexpr (TC) {  // MMA 1 / MMA 2 completion
-            mbar_init(smem_u32(&bars[2 * NSLOT + 4]), 1);
-            mbar_init(smem_u32(&bars[2 * NSLOT + 5]), 1);
+        if constexpr (TC) {
+            mbar_init(smem_u32(&bars[2 * NSLOT + 4]), 1);         // MMA 1 complete (tcgen05.commit)
+            mbar_init(smem_u32(&bars[2 * NSLOT + 5]), 1);         // MMA 2 complete
+            mbar_init(smem_u32(&bars[2 * NSLOT + 6]), C::NFFTT);  // step-1 operand written
+            mbar_init(smem_u32(&bars[2 * NSLOT + 7]), C::NFFTT);  // step-2 operand written
         }
         mbar_init_fence();
         *abort_flag = 0;
@@ -649,9 +680,9 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
         const int ft = threadIdx.x - C::NFT;
         if constexpr (TC) {
-            ws_tc_dft<C>(a, range, ws_smem, meta, yfull0, yempty0, smem_u32(&bars[2 * NSLOT + 4]),
-                         smem_u32(&bars[2 * NSLOT + 5]), *tmem_slot,
-                         abort_flag, ft, warp, lane);
+            ws_tc_dft<C>(a, range, ws_smem, meta, yfull0, yempty0, smem_u32(&bars[2 * NSLOT + 6]),
+                         smem_u32(&bars[2 * NSLOT + 7]), smem_u32(&bars[2 * NSLOT + 4]),
+                         smem_u32(&bars[2 * NSLOT + 5]), *tmem_slot, abort_flag, ft, warp, lane);
         } else {
         uint32_t bc = 0;
         bool ok = true;
@@ -689,6 +720,12 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
     } else {
         // ======================= producer warp(group) =======================
         if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
+        if constexpr (TC) {
+            if (warp == C::PRODW + 1 && lane == 0)
+                ws_tc_mma_thread<C>(a, range, ws_smem, smem_u32(&bars[2 * NSLOT + 6]), smem_u32(&bars[2 * NSLOT + 7]),
+                                    smem_u32(&bars[2 * NSLOT + 4]), smem_u32(&bars[2 * NSLOT + 5]), *tmem_slot,
+                                    abort_flag);
+        }
         if (warp == C::PRODW && lane == 0) {
             uint32_t pc = 0;
             bool ok = true;
