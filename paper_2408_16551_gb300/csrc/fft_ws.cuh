@@ -102,8 +102,11 @@ struct WsCfg {
     static_assert(NFT % 128 == 0 || !SETMAXNREG, "FIR warps form whole warpgroups");
     static_assert(!DIF4 || (NB == 4 && NFT == Q && fft_npasses(Q, MR) == 2), "DIF4 layout");
     static_assert(NFIRW * 32 + NFFTT + (SETMAXNREG ? 128 : 32) == NTHREADS, "layout");
-    // register split (setmaxnreg): FIR 208, FFT 72, producer warpgroup 24
-    static_assert(!SETMAXNREG || NFT * 208 + NFFTT * 72 + 128 * 24 <= NTHREADS * (65536 / NTHREADS), "registers");
+    // register split (setmaxnreg): FIR 208, FFT 72, producer warpgroup 24; the
+    // tensor-core DFT warps (TC) keep more live values, their FIR is lighter
+    static constexpr int REG_FIR = TC ? 200 : 208, REG_FFT = TC ? 88 : 72, REG_PROD = 24;
+    static_assert(!SETMAXNREG || NFT * REG_FIR + NFFTT * REG_FFT + 128 * REG_PROD <= NTHREADS * (65536 / NTHREADS),
+                  "registers");
 };
 
 struct WsMeta {
@@ -424,15 +427,18 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
             }
             // ---- twiddle, split, transposed store: MMA 2 operand row (q, k1), K = (n2 = lane, re/im) ----
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t r[32];
-                tmem_ld32(trow + kTcColD1 + 32 * h, r);
+            for (int h = 0; h < 4; ++h) {  // 8 k1 per TMEM load
+                // the twiddles first: the operand stores below may alias them for the compiler
+                float2 w8[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) w8[j] = twt[(8 * h + j) * C::TC_P1 + lane];
+                uint32_t r[16];
+                tmem_ld16(trow + kTcColD1 + 16 * h, r);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int k1 = 16 * h + j;
-                    const float2 z = cmul(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])),
-                                          twt[k1 * C::TC_P1 + lane]);
+                for (int j = 0; j < 8; ++j) {
+                    const int k1 = 8 * h + j;
+                    const float2 z = cmul(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])), w8[j]);
                     uint32_t hi, lo;
                     split_bf16x2(z, hi, lo);
                     const int off = a2_base + (k1 >> 3) * 128 + (k1 & 7) * 16;
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
 
     if (warp < C::NFIRW) {
         // ======================= FIR warps =======================
-        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
+        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::REG_FIR) : "memory");
         const int t = threadIdx.x;
         constexpr int NPAIR = C::NPAIR;
         constexpr int PSTRIDE = P / NPAIR;   // distance between this thread's branch pairs
@@ -677,7 +683,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         }
     } else if (warp < C::PRODW) {
         // ======================= FFT warps =======================
-        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
+        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::REG_FFT) : "memory");
         const int ft = threadIdx.x - C::NFT;
         if constexpr (TC) {
             ws_tc_dft<C>(a, range, ws_smem, meta, yfull0, yempty0, smem_u32(&bars[2 * NSLOT + 6]),
@@ -719,7 +725,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         }
     } else {
         // ======================= producer warp(group) =======================
-        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
+        if constexpr (C::SETMAXNREG) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::REG_PROD) : "memory");
         if constexpr (TC) {
             if (warp == C::PRODW + 1 && lane == 0)
                 ws_tc_mma_thread<C>(a, range, ws_smem, smem_u32(&bars[2 * NSLOT + 6]), smem_u32(&bars[2 * NSLOT + 7]),
