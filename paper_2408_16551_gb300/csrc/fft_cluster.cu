@@ -5,10 +5,10 @@ namespace pfb {
 
 int64_t cluster_units(int64_t S) { return (S + 7) / 8; }
 
-template <int CS, int TT, int IN>
+template <int CS, int TT, int IN, bool TC>
 static pfb_status launch_cluster_k(LaunchArgs &a, cudaStream_t stream) {
-    using C = ClusterCfg<CS>;
-    auto k = k_fft_cluster<CS, TT, IN>;
+    using C = ClusterCfg<CS, TC>;
+    auto k = k_fft_cluster<CS, TT, IN, TC>;
     static int cap_clusters = 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -45,18 +45,18 @@ static pfb_status launch_cluster_k(LaunchArgs &a, cudaStream_t stream) {
     return PFB_OK;
 }
 
-template <int CS>
+template <int CS, bool TC>
 static pfb_status launch_cluster_cs(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     switch (plan.in_dtype * 100 + plan.TT) {
-    case PFB_IN_C64 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_C64>(a, stream);
-    case PFB_IN_C64 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_C64>(a, stream);
-    case PFB_IN_C64 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_C64>(a, stream);
-    case PFB_IN_R32 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_R32>(a, stream);
-    case PFB_IN_R32 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_R32>(a, stream);
-    case PFB_IN_R32 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_R32>(a, stream);
-    case PFB_IN_CI8 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_CI8>(a, stream);
-    case PFB_IN_CI8 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_CI8>(a, stream);
-    case PFB_IN_CI8 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_CI8>(a, stream);
+    case PFB_IN_C64 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_C64, TC>(a, stream);
+    case PFB_IN_C64 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_C64, TC>(a, stream);
+    case PFB_IN_C64 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_C64, TC>(a, stream);
+    case PFB_IN_R32 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_R32, TC>(a, stream);
+    case PFB_IN_R32 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_R32, TC>(a, stream);
+    case PFB_IN_R32 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_R32, TC>(a, stream);
+    case PFB_IN_CI8 * 100 + 4: return launch_cluster_k<CS, 4, PFB_IN_CI8, TC>(a, stream);
+    case PFB_IN_CI8 * 100 + 8: return launch_cluster_k<CS, 8, PFB_IN_CI8, TC>(a, stream);
+    case PFB_IN_CI8 * 100 + 16: return launch_cluster_k<CS, 16, PFB_IN_CI8, TC>(a, stream);
     default: return fail(PFB_ERR_UNSUPPORTED, "cluster FFT family: no kernel for this T/dtype");
     }
 }
@@ -66,9 +66,21 @@ bool fft_cluster_supported(int P, int T) { return (P == 2048 || P == 4096) && T 
 pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     a.aux = plan.d_tw_r2;
     switch (plan.P) {
-    case 2048: return launch_cluster_cs<2>(plan, a, stream);
-    case 4096: return launch_cluster_cs<4>(plan, a, stream);
+    case 2048: return launch_cluster_cs<2, false>(plan, a, stream);
+    case 4096: return launch_cluster_cs<4, false>(plan, a, stream);
     default: return fail(PFB_ERR_UNSUPPORTED, "cluster FFT family: P must be 2048 or 4096");
+    }
+}
+
+// the same cluster kernel with its local 1024-point DFT on the tensor cores
+// (factored split-bf16 route for P = 2048, 4096)
+pfb_status launch_fft_cluster_tc(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    a.aux = plan.d_tw_r2;
+    a.tw = static_cast<const float2 *>(plan.d_tcf);
+    switch (plan.P) {
+    case 2048: return launch_cluster_cs<2, true>(plan, a, stream);
+    case 4096: return launch_cluster_cs<4, true>(plan, a, stream);
+    default: return fail(PFB_ERR_UNSUPPORTED, "factored split-bf16 DFT on a cluster: P must be 2048 or 4096");
     }
 }
 

@@ -1,14 +1,23 @@
-// Split-bf16 DFT on the tensor cores in factored (four-step) form, P = 32 x 32
-// (variant 1 of the split-bf16 family): the warp-specialised FIR front end of
-// fft_ws.cuh feeding two 32-point DFT-matrix products (Sec. 4.1 DFT as a
-// matrix product, split into bf16 hi/lo terms).  Executed tensor work is
+// Split-bf16 DFT on the tensor cores in factored (four-step) form (variant 1
+// of the split-bf16 family).  P = 1024 = 32 x 32: the warp-specialised FIR
+// front end of fft_ws.cuh feeding two 32-point DFT-matrix products (Sec. 4.1
+// DFT as a matrix product, split into bf16 hi/lo terms).  P = 2048, 4096: the
+// cluster kernel (fft_cluster.cuh) with its local 1024-point DFT done the same
+// way after the cross-CTA radix-CS step.  Executed tensor work is
 // 2 x 3 x 8 x 32 = 1536 bf16 flop per sample instead of 24 P for the dense
 // DFT-matrix product, and the FIR runs once per spectrum.
 #include "fft_fast.cuh"  // ypad and the warp-specialised kernel (fft_ws.cuh)
 
 namespace pfb {
 
-bool tcf_supported(const Plan &plan) { return plan.P == 1024 && plan.T == plan.TT && plan.TT <= 16; }
+// P = 1024: the warp-specialised streaming kernel (T must equal a compiled tap
+// count); P = 2048, 4096: the cluster kernel (any T <= 16, taps zero-padded)
+bool tcf_supported(const Plan &plan) {
+    if (plan.P == 1024) return plan.T == plan.TT && plan.TT <= 16;
+    return (plan.P == 2048 || plan.P == 4096) && plan.T <= 16;
+}
+
+pfb_status launch_fft_cluster_tc(const Plan &plan, LaunchArgs &a, cudaStream_t stream);
 
 // tables: B_hi, B_lo (64 x 64 bf16 each, K-major core-matrix tiles, K = 2 n1 + c_in,
 // N = 2 k1 + c_out, real block form of w_32^(n1 k1)), then w_1024^(k1 n2) as [k1][n2]
@@ -46,7 +55,9 @@ pfb_status build_tcf_table(Plan &plan) {
 }
 
 pfb_status launch_gemm_bf16x3_tcf(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
-    if (!tcf_supported(plan)) return fail(PFB_ERR_UNSUPPORTED, "factored split-bf16 DFT needs P = 1024, T in {4, 8, 16}");
+    if (!tcf_supported(plan))
+        return fail(PFB_ERR_UNSUPPORTED, "factored split-bf16 DFT needs P = 1024 with T in {4, 8, 16}, or P = 2048, 4096");
+    if (plan.P != 1024) return launch_fft_cluster_tc(plan, a, stream);
     for (int i = 0; i < a.nstreams; ++i)
         if (a.s[i].T != plan.TT) return fail(PFB_ERR_UNSUPPORTED, "factored split-bf16 DFT: T mismatch");
     a.aux = plan.d_tcf;

@@ -59,8 +59,10 @@ constexpr int K2_CHUNK = 8;                        // K blocks per TMEM accumula
 constexpr uint32_t K2_IDESC = tc_idesc_bf16(K2_M, K2_N);
 
 // variant 0: (128-spectrum M tile, 128-bin N tile) pairs; variant 1 (factored): spectra
+int64_t cluster_units(int64_t S);
+
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) {
-    if (plan.variant == 1) return S;
+    if (plan.variant == 1) return plan.P == 1024 ? S : cluster_units(S);
     return ((S + K2_M - 1) / K2_M) * (plan.P / (K2_N / 2));
 }
 

@@ -138,6 +138,8 @@ def test_factored_is_the_default_at_p1024():
         plan2.variant = 1
     plan3 = pkg.Plan(512, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
     assert plan3.variant == 0
+    for P, T in ((2048, 16), (4096, 12)):   # cluster route: any T <= 16
+        assert pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3).variant == 1
 
 
 @pytest.mark.parametrize("T,dt,rows", [(16, synth.IN_C64, 4 * 37 + 3), (8, synth.IN_CI8, 4 * 20 + 1),
@@ -195,3 +197,38 @@ def test_gemm_bf16x3_factored_batch_and_c2_sample():
     xin = oracle.dequant(x, oracle.IN_C64)
     ref = np.stack([oracle.dft(oracle.fir(xin, P, T, h, s0=r, ns=1))[0] for r in rows])
     assert oracle.rel_l2(got, ref) < TOL_BF16X3
+
+
+@pytest.mark.parametrize("P,T,dt,rows", [(4096, 16, synth.IN_C64, 8 * 5 + 3), (2048, 8, synth.IN_CI8, 8 * 9 + 7),
+                                         (4096, 12, synth.IN_R32, 8 * 3), (2048, 16, synth.IN_C64, 5)])
+def test_gemm_bf16x3_factored_cluster_parity(P, T, dt, rows):
+    """P = 2048 / 4096: cross-CTA radix-CS step, then the local 1024-point DFT as
+    two tensor-core products; several 8-spectrum units with ragged tails."""
+    n = P * (T - 1 + rows) + 11
+    plan, x, got = _run_variant(1, P, T, dt, n, seed=P + T + rows)
+    ref = reference(x, dt, P, T, synth.WIN_HANN)
+    assert got.shape == ref.shape == (rows, P)
+    e2, em = assert_close(got, ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"bf16x3 factored P={P} T={T}")
+    assert e2 > 1e-8
+
+
+def test_gemm_bf16x3_factored_c3_sample():
+    """c3 (64 streams x 2^20, P = 4096, T = 16, Blackman) as one batched launch on the
+    factored tensor-core route: sampled spectra of two streams against the oracle."""
+    import torch
+    specs = synth.config_c3()
+    P, T, win = specs[0].P, specs[0].T, specs[0].window
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, win, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan.variant == 1
+    xs_host = [sp.generate() for sp in specs]
+    xs = [to_device(x) for x in xs_host]
+    S = plan.out_spectra(xs_host[0].size)
+    outs = [torch.empty((S, P), dtype=torch.complex64, device="cuda") for _ in xs]
+    pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xs, outs)])
+    torch.cuda.synchronize()
+    h = oracle.prototype(P, T, win)
+    for i in (0, 41):
+        rows = [0, 1, S // 2, S - 1]
+        xin = oracle.dequant(xs_host[i], oracle.IN_C64)
+        ref = np.stack([oracle.dft(oracle.fir(xin, P, T, h, s0=r, ns=1))[0] for r in rows])
+        assert oracle.rel_l2(outs[i][rows].cpu().numpy(), ref) < TOL_BF16X3
