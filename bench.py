@@ -386,7 +386,9 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the c3/c4 lines")
     ap.add_argument("--minimal", action="store_true", help="headline timing only (for profiler runs)")
     ap.add_argument("--nsets", type=int, default=4, help="rotating input/output buffer sets")
-    ap.add_argument("--variant", type=int, default=-1, help="kernel variant of the FFT path (-1: autotune)")
+    ap.add_argument("--variant", type=int, default=-1, help="kernel variant of the headline path (-1: autotune / default)")
+    ap.add_argument("--path", default="fft", choices=["fft", "bf16x3"],
+                    help="DFT route of the headline step: FP32 FFT, or the split-bf16 tensor-core DFT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -412,12 +414,14 @@ def main():
     spec, x = workload_c2()
     P, T = spec.P, spec.T
     n = int(x.size)
-    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_FFT_F32)
+    tc_path = args.path == "bf16x3"
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_GEMM_BF16X3 if tc_path else pkg.PFB_DFT_FFT_F32)
     S = plan.out_spectra(n)
     if args.variant >= 0:
         plan.variant = args.variant
-    else:
+    elif not tc_path:
         plan.autotune(n)  # tile shape (kernel variant) from the autotuner
+    # (split-bf16: the factored tensor-core DFT is the plan's default variant at P = 1024)
     nsets = max(1, args.nsets)  # rotating input/output sets: 4 x 256 MiB > 129 MB L2
     xd0 = torch.from_numpy(x).to(device)
     xs = [xd0] + [xd0.clone() for _ in range(nsets - 1)]
@@ -471,14 +475,23 @@ def main():
                 "traffic": traffic, "kernel": f"{plan.kernel_name} variant {plan.variant}",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    if tc_path and plan.variant == 1:
+        # executed bf16 tensor work of the factored DFT per spectrum: 2 products
+        # (32 rows x 64 x 64 real block form each) x 3 split terms x 2 flop/MAC
+        # = 1,572,864 flop per 1024 samples = 1536 flop per sample
+        flop = n * (2 * 3 * 2 * 32 * 64 * 64 // 1024)
+        tfl = flop / (kern_ms * 1e-3) / 1e12
+        roofline["tensor"] = {"executed_tflops": tfl, "peak_tflops": bf16s, "frac": tfl / bf16s,
+                              "flop_per_sample": flop // n, "peak_source": "sustained bf16 (MEASURED_PEAKS.json)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3/f32acc" if tc_path else "f32", "data": "synthetic",
         "config": {"workload": "c2: one stream of 2^24 complex64 samples (CN(0,1) + 8 channel-centre tones), "
-                               "P=1024, T=16, Hamming-windowed sinc prototype; FIR + FFT path (FP32)",
-                   "P": P, "T": T, "n_samples": n, "spectra": S, "path": "fft_f32",
+                               "P=1024, T=16, Hamming-windowed sinc prototype; "
+                               + ("FIR + split-bf16 tensor-core DFT path" if tc_path else "FIR + FFT path (FP32)"),
+                   "P": P, "T": T, "n_samples": n, "spectra": S, "path": "gemm_bf16x3" if tc_path else "fft_f32",
                    "variant": plan.variant,
                    "l2": f"{nsets} rotating input/output buffer sets ({nsets * (n * 8 + S * P * 8) >> 20} MiB) > 129 MB L2",
                    "replicas": "each rank channelises its own copy of the workload (weak scaling, no collective)"},
@@ -490,14 +503,18 @@ def main():
     if not args.minimal:
         import numpy as np
         rows = sorted(set([0, S // 3, S // 2, S - 1] + list(np.random.default_rng(1).integers(0, S, 6))))
-        paths = {"fft_f32": {"gsps": value / world, "rel_l2": sampled_rel_l2(outs[(args.steps - 1) % nsets], x,
-                                                                           spec.in_dtype, P, T, spec.window, rows),
-                             "dtype": "f32", "kernel": plan.kernel_name}}
+        head = "gemm_bf16x3" if tc_path else "fft_f32"
+        paths = {head: {"gsps": value / world, "rel_l2": sampled_rel_l2(outs[(args.steps - 1) % nsets], x,
+                                                                       spec.in_dtype, P, T, spec.window, rows),
+                        "dtype": "bf16x3/f32acc" if tc_path else "f32", "kernel": plan.kernel_name}}
+        others = (("fft_f32", pkg.PFB_DFT_FFT_F32, "f32"),) if tc_path else \
+            (("gemm_bf16x3", pkg.PFB_DFT_GEMM_BF16X3, "bf16x3/f32acc"),)
         if not args.no_paths:
-            for name, path, dt in (("gemm_bf16x3", pkg.PFB_DFT_GEMM_BF16X3, "bf16x3/f32acc"),
-                                   ("gemm_f32", pkg.PFB_DFT_GEMM_F32, "f32")):
+            for name, path, dt in others + (("gemm_f32", pkg.PFB_DFT_GEMM_F32, "f32"),):
                 try:
                     p2 = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, path)
+                    if path == pkg.PFB_DFT_FFT_F32:
+                        p2.autotune(n)
                     ms, per = time_path(pkg, p2, xs, outs, max(3, args.steps // 4), 2, stream)
                     err = sampled_rel_l2(outs[(max(3, args.steps // 4) - 1) % nsets], x, spec.in_dtype, P, T,
                                          spec.window, rows)
