@@ -111,13 +111,24 @@ pfb_status build_gemm_bf16x3_table(Plan &plan) {
 
 pfb_status build_gemm_f32_table(Plan &plan);
 
+// tables a variant needs that plan creation did not build
+pfb_status ensure_variant_tables(Plan &plan) {
+    if (plan.family == FAM_GEMM_BF16X3 && plan.variant == 0 && !plan.d_dft && plan.P >= K2_N / 2 && plan.T <= 16) {
+        pfb_status st = build_gemm_bf16x3_table(plan);
+        if (st != PFB_OK) return st;
+        PFB_CUDA_TRY(cudaDeviceSynchronize());
+    }
+    return PFB_OK;
+}
+
 pfb_status build_gemm_tables(Plan &plan) {
     if (plan.family == FAM_GEMM_F32) return build_gemm_f32_table(plan);
     if (plan.family == FAM_GEMM_BF16X3) {
         if (plan.P < K2_N / 2 || plan.T > 16) return PFB_OK;  // no kernel; execute reports UNSUPPORTED
         if (tcf_supported(plan)) {
-            pfb_status st = build_tcf_table(plan);
-            if (st != PFB_OK) return st;
+            // the dense DFT matrix (16 MB at P = 1024, 256 MB at P = 4096) is
+            // built only when its variant is selected (ensure_variant_tables)
+            return build_tcf_table(plan);
         }
         return build_gemm_bf16x3_table(plan);
     }
@@ -428,6 +439,7 @@ pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &a, cudaStream_t stre
     if (plan.variant == 1) return launch_gemm_bf16x3_tcf(plan, a, stream);
     if (plan.P < K2_N / 2) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs P >= 128");
     if (plan.T > 16) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs T <= 16");
+    if (a.nunits > 0 && !plan.d_dft) return fail(PFB_ERR_INTERNAL, "split-bf16 DFT matrix not built");
     switch (plan.in_dtype) {
     case PFB_IN_C64: return launch_k2_t<PFB_IN_C64>(plan, a, stream);
     case PFB_IN_R32: return launch_k2_t<PFB_IN_R32>(plan, a, stream);

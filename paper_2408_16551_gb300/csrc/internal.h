@@ -130,6 +130,7 @@ pfb_status build_tcf_table(Plan &plan);
 pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 bool fft_cluster_supported(int P, int T);
 pfb_status prepare_family(const Plan &plan);
+pfb_status ensure_variant_tables(Plan &plan);
 const float *family_taps(const Plan &plan);   // tap layout the family's kernels read
 // work units a stream of S spectra contributes to a launch of the plan's family
 int64_t family_units(const Plan &plan, int64_t S);

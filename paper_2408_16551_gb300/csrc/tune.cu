@@ -126,6 +126,8 @@ extern "C" pfb_status pfb_plan_set_variant(pfb_plan_t plan, int32_t variant) {
     if (variant < 0 || variant >= family_variants(p)) return fail(PFB_ERR_INVALID, "variant out of range");
     if (!variant_supported(p, variant)) return fail(PFB_ERR_UNSUPPORTED, "variant not available for this P/T");
     p.variant = variant;
+    pfb_status st = ensure_variant_tables(p);
+    if (st != PFB_OK) return st;
     return prepare_family(p);
 }
 
@@ -156,7 +158,8 @@ extern "C" pfb_status pfb_plan_autotune(pfb_plan_t plan, int64_t n_samples, void
     for (int v = 0; st == PFB_OK && v < nv; ++v) {
         if (!variant_supported(p, v)) continue;
         p.variant = v;
-        st = prepare_family(p);
+        st = ensure_variant_tables(p);
+        if (st == PFB_OK) st = prepare_family(p);
         if (st != PFB_OK) break;
         for (int w = 0; w < 2 && st == PFB_OK; ++w) st = pfb_execute(plan, din, n_samples, dout, S, s);
         if (st != PFB_OK) break;
