@@ -137,6 +137,37 @@ PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samp
 PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples,
                             void *host_out, int64_t out_cap_spectra, void *cuda_stream);
 
+/* Size of the static device staging area of pfb_execute_host_noalloc. */
+#define PFB_NOALLOC_SCRATCH_BYTES (32ll << 20)
+
+/* pfb_execute_host that allocates nothing.  The paper has no counterpart: it
+ * exists for callers that must not allocate device memory -- a process whose
+ * device memory is owned by another allocator (a framework's caching pool, a
+ * fixed reservation), or a latency-critical thread that cannot take the
+ * device-wide synchronisation cudaMalloc/cudaFree may imply -- while
+ * pfb_execute_host grows plan-owned staging buffers with cudaMalloc and
+ * creates copy streams and events.
+ * Same arguments and results as pfb_execute_host (host_in, host_out in host
+ * memory; pinned memory copies fastest).  The whole frames of the input and
+ * the S output spectra are staged through one fixed area of static device
+ * memory, PFB_NOALLOC_SCRATCH_BYTES (32 MiB) per device, held by every device
+ * that loads the library until the process exits: input at offset 0, output
+ * at the next multiple of 256 bytes.  Copy in, kernel and copy out run in
+ * order on cuda_stream (after the work already queued there); the call
+ * returns once host_out is written.  No cudaMalloc, cudaFree, stream or event
+ * creation happens in the call.
+ *  - The first call on a device looks up the area's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture begins.
+ *  - Every call on a device shares the one area, which keeps the last call's
+ *    contents.  Calls whose work overlaps on the GPU (several host threads,
+ *    or several streams) race on it: serialise them.
+ * Errors: as pfb_execute_host; PFB_ERR_INVALID also when the staged input
+ * (rounded up to 256 bytes) plus the output exceed PFB_NOALLOC_SCRATCH_BYTES,
+ * with nothing launched. */
+PFB_API pfb_status pfb_execute_host_noalloc(pfb_plan_t plan, const void *host_in, int64_t n_samples,
+                                            void *host_out, int64_t out_cap_spectra, void *cuda_stream);
+
 /* One stream of a batch. */
 typedef struct pfb_batch_item {
     pfb_plan_t plan;

@@ -29,6 +29,7 @@ PFB_ERR_TIMEOUT, PFB_ERR_INTERNAL, PFB_ERR_UNSUPPORTED = -5, -6, -7
 PFB_IN_R32, PFB_IN_C64, PFB_IN_CI8 = 0, 1, 2
 PFB_WIN_HANN, PFB_WIN_HAMMING, PFB_WIN_BLACKMAN, PFB_WIN_USER = 0, 1, 2, 3
 PFB_DFT_FFT_F32, PFB_DFT_GEMM_F32, PFB_DFT_GEMM_BF16X3 = 0, 1, 2
+NOALLOC_SCRATCH_BYTES = 32 << 20  # PFB_NOALLOC_SCRATCH_BYTES
 
 EXPORTED = [
     "pfb_plan_create", "pfb_plan_destroy", "pfb_out_spectra", "pfb_plan_get_taps", "pfb_execute",
@@ -37,6 +38,7 @@ EXPORTED = [
     "pfb_stream_next_spectra", "pfb_submit", "pfb_poll", "pfb_wait", "pfb_server_get_stats",
     "pfb_status_string", "pfb_last_error", "pfb_launch_count", "pfb_plan_kernel_name",
     "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
+    "pfb_execute_host_noalloc",
 ]
 
 
@@ -98,6 +100,7 @@ def lib() -> ctypes.CDLL:
             "pfb_plan_get_taps": (st, [vp, ctypes.POINTER(ctypes.c_double), i64]),
             "pfb_execute": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_execute_host": (st, [vp, vp, i64, vp, i64, vp]),
+            "pfb_execute_host_noalloc": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_execute_batch": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
             "pfb_batch_create": (st, [ctypes.POINTER(pfb_batch_item), i32, ctypes.POINTER(vp)]),
             "pfb_batch_launch": (st, [vp, vp]),
@@ -248,6 +251,19 @@ class Plan:
         _check(lib().pfb_execute_host(self.handle, ctypes.c_void_p(x.ctypes.data), n,
                                       ctypes.c_void_p(out.ctypes.data), out.size // self.P,
                                       _stream_handle(stream)), "pfb_execute_host")
+        return out
+
+    def execute_host_noalloc(self, x: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """pfb_execute_host_noalloc: as execute_host, staged through the library's
+        static device area (no device allocation; input + output at most
+        NOALLOC_SCRATCH_BYTES)."""
+        n = x.size // 2 if self.in_dtype == PFB_IN_CI8 else x.size
+        S = self.out_spectra(n)
+        if out is None:
+            out = np.empty((S, self.P), dtype=np.complex64)
+        _check(lib().pfb_execute_host_noalloc(self.handle, ctypes.c_void_p(x.ctypes.data), n,
+                                              ctypes.c_void_p(out.ctypes.data), out.size // self.P,
+                                              _stream_handle(stream)), "pfb_execute_host_noalloc")
         return out
 
 
