@@ -28,7 +28,7 @@ int64_t generic_units(int P, int64_t S);
 int64_t fast_units(const Plan &plan, int64_t S);
 int64_t gemm_f32_units(const Plan &plan, int64_t S);
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S);
-int64_t cluster_units(int64_t S);
+int64_t fft_cluster_units(const Plan &plan, int64_t S);
 
 int64_t family_units(const Plan &plan, int64_t S) {
     switch (plan.family) {
@@ -36,7 +36,7 @@ int64_t family_units(const Plan &plan, int64_t S) {
     case FAM_FFT_GENERIC: return generic_units(plan.P, S);
     case FAM_GEMM_F32: return gemm_f32_units(plan, S);
     case FAM_GEMM_BF16X3: return gemm_bf16x3_units(plan, S);
-    case FAM_FFT_CLUSTER: return cluster_units(S);
+    case FAM_FFT_CLUSTER: return fft_cluster_units(plan, S);
     default: return 0;
     }
 }

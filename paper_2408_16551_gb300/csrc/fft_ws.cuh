@@ -615,8 +615,6 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                     }
                                 }
                             }
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
                         }
                         ++pc;
                         // ---- feed the T spectra this frame belongs to ----
@@ -632,6 +630,13 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                     pend[js][b] = fma2(make_float2(h[m][b], h[m][b]), v[b], pend[js][b]);
                                 }
                             }
+                        }
+                        // the ring slot goes back to the producer only now that every
+                        // lane has used the values it loaded from it (a TMA refill must
+                        // not overtake a shared-memory read still in flight)
+                        if (ok) {
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
                         }
                         // ---- spectrum i - TT + 1 is complete ----
                         const int64_t jspec = i - (TT - 1);

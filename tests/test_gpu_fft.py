@@ -287,3 +287,67 @@ def test_ws_variant_streams_and_batches(P, T):
     for (plan, xd, out), ref in zip(entries, singles):
         if ref is not None:
             assert torch.equal(out[:ref.shape[0]], ref)
+
+
+WS_CLUSTER = [(4096, 16, synth.IN_C64, 43), (2048, 16, synth.IN_CI8, 43), (4096, 8, synth.IN_R32, 301),
+              (2048, 4, synth.IN_C64, 1000), (4096, 4, synth.IN_CI8, 7), (4096, 16, synth.IN_C64, 1001),
+              (2048, 8, synth.IN_R32, 1)]
+
+
+@pytest.mark.parametrize("P,T,dt,S", WS_CLUSTER)
+def test_cluster_variants_match_oracle(P, T, dt, S):
+    """P = 2048 / 4096 on a CTA cluster: variant 0 (synchronous) and variant 1
+    (warp-specialised, TMA ring, cross-CTA mbarriers) against the oracle, and
+    variant 1 bitwise reproducible."""
+    import torch
+    n = P * (S + T - 1) + 5
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=P + S).generate()
+    ref = reference(x, dt, P, T, synth.WIN_BLACKMAN)
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_BLACKMAN)
+    assert plan.num_variants == 2 and plan.variant == 1
+    xd = to_device(x)
+    outs = []
+    for v in (0, 1):
+        plan.variant = v
+        X = plan.execute(xd)
+        torch.cuda.synchronize()
+        outs.append(X.cpu().numpy())
+        assert_close(outs[-1], ref, what=f"cluster variant {v} P={P} T={T} dt={dt} S={S}")
+    for _ in range(4):  # a ring slot refilled too early shows up as a run of wrong spectra
+        again = plan.execute(xd).cpu().numpy()
+        assert np.array_equal(again, outs[1])
+
+
+def test_cluster_ws_batch_equals_single():
+    """Uneven streams (some with 0 spectra) of one P = 4096 plan in one batched
+    launch of the warp-specialised cluster kernel: identical to per-stream runs."""
+    import torch
+    P, T = 4096, 16
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN)
+    assert plan.variant == 1
+    lens = [P * 20 + 3, P * 3, P * 15, P * 97 + 11, P * 16, P * 300, P * 41]
+    xs = [to_device(synth.small_stream(P, T, n, seed=70 + i).generate()) for i, n in enumerate(lens)]
+    singles = [plan.execute(x).clone() if plan.out_spectra(x.numel()) > 0 else None for x in xs]
+    outs = [torch.full((max(plan.out_spectra(x.numel()), 1), P), 9.0, dtype=torch.complex64, device="cuda")
+            for x in xs]
+    pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xs, outs)])
+    torch.cuda.synchronize()
+    for s, o in zip(singles, outs):
+        if s is not None:
+            assert torch.equal(o[:s.shape[0]], s)
+        else:
+            assert torch.all(o == 9.0)
+
+
+@pytest.mark.parametrize("variant", [5])
+def test_ws_repeatable_at_scale(variant):
+    """The warp-specialised P = 1024 kernel over 4096 spectra, run six times:
+    bitwise identical (a race on the TMA ring would corrupt runs of spectra)."""
+    import torch
+    P, T = 1024, 16
+    xd = to_device(synth.small_stream(P, T, P * (4096 + T - 1), seed=17).generate())
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HAMMING)
+    plan.variant = variant
+    a = plan.execute(xd).clone()
+    for _ in range(5):
+        assert torch.equal(plan.execute(xd), a)
