@@ -61,7 +61,10 @@ struct WcCfg {
     static constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
     static constexpr int FB = PL * ESZ;             // bytes of the CTA's slice of a frame
     static constexpr int NTQ = fft_tw_entries(Q, MR);
-    static constexpr int NTW = NTQ + 3 * Q;
+    // pass list, pre-twiddles w_PL^(n' k1'), then the cross-step twiddles
+    // w_P^(n k1) of this CTA's n = c*QC + nl + Q j, as [k1 - 1][j][nl]
+    static constexpr int NTX = (CS - 1) * 4 * QC;
+    static constexpr int NTW = NTQ + 3 * Q + NTX;
     // gather buffer X of the cross step: [s][n1][j pair][n' - c*QC], 16 bytes
     // (two branch sums, j = 2 jp and 2 jp + 1) per entry
     static constexpr int XBUF = SB * CS * 2 * QC;   // 16-byte entries per buffer
@@ -198,6 +201,10 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
         }
         for (int i = threadIdx.x; i < 3 * Q; i += C::NTHREADS)
             tw[C::NTQ + i] = tw_full(tw_half, CS * (i % Q) * (i / Q + 1), P);
+        for (int i = threadIdx.x; i < C::NTX; i += C::NTHREADS) {
+            const int nl = i % QC, j = (i / QC) % 4, k1 = i / (4 * QC) + 1;
+            tw[C::NTQ + 3 * Q + i] = tw_full(tw_half, ((int)crank * QC + nl + Q * j) * k1, P);
+        }
     }
     __syncthreads();
     cluster_sync_all();  // barriers of every CTA initialised and armed before any remote traffic
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
         // ======================= FFT warps =======================
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::REG_FFT) : "memory");
         const int ft = threadIdx.x - NFT;
-        const float2 *tw_half = static_cast<const float2 *>(a.aux);
+        const float2 *twx = tw + C::NTQ + 3 * Q;  // cross-step twiddles [k1 - 1][j][nl]
         const uint32_t zloc = smem_u32(Z);
         uint32_t bc = 0;
         bool ok = true;
@@ -358,29 +365,29 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
 #pragma unroll
                         for (int h2 = 0; h2 < 2; ++h2) {
                             const int j = 2 * jp + h2;
-                            const int n = np + Q * j;
                             float2 u[CS];
 #pragma unroll
                             for (int n1 = 0; n1 < CS; ++n1)
                                 u[n1] = h2 == 0 ? make_float2(e[n1].x, e[n1].y) : make_float2(e[n1].z, e[n1].w);
-                            dft_reg<CS, false>(u);
+                            dft_reg<CS, true>(u);
                             z[0][j] = u[0];
 #pragma unroll
-                            for (int k1 = 1; k1 < CS; ++k1) z[k1][j] = cmul(u[k1], tw_full(tw_half, n * k1, P));
+                            for (int k1 = 1; k1 < CS; ++k1) z[k1][j] = cmul(u[k1], twx[((k1 - 1) * 4 + j) * QC + nl]);
                         }
                     }
                     const uint32_t zoff = (uint32_t)(4 * s * SROW + ypad<G>(np)) * 8u;
 #pragma unroll
                     for (int k1 = 0; k1 < CS; ++k1) {
                         // radix-4 butterfly over j (the twiddles w_PL^(n' k1') come in pass 1)
-                        const float2 a0 = cadd(z[k1][0], z[k1][2]), a1 = csub(z[k1][0], z[k1][2]);
-                        const float2 a2 = cadd(z[k1][1], z[k1][3]), a3 = csub(z[k1][1], z[k1][3]);
+                        const float2 a0 = cadd2(z[k1][0], z[k1][2]), a1 = csub2(z[k1][0], z[k1][2]);
+                        const float2 a2 = cadd2(z[k1][1], z[k1][3]), a3 = csub2(z[k1][1], z[k1][3]);
+                        const float2 mi_a3 = make_float2(a3.y, -a3.x);  // -i a3
                         const uint32_t zb = mapa_shared(zloc + zoff, k1);
                         const uint32_t zfb = mapa_shared(zf_base, k1);
-                        st_async_v2(zb, cadd(a0, a2), zfb);
-                        st_async_v2(zb + SROW * 8u, make_float2(a1.x + a3.y, a1.y - a3.x), zfb);
-                        st_async_v2(zb + 2u * SROW * 8u, csub(a0, a2), zfb);
-                        st_async_v2(zb + 3u * SROW * 8u, make_float2(a1.x - a3.y, a1.y + a3.x), zfb);
+                        st_async_v2(zb, cadd2(a0, a2), zfb);
+                        st_async_v2(zb + SROW * 8u, cadd2(a1, mi_a3), zfb);
+                        st_async_v2(zb + 2u * SROW * 8u, csub2(a0, a2), zfb);
+                        st_async_v2(zb + 3u * SROW * 8u, csub2(a1, mi_a3), zfb);
                     }
                 }
                 // our X buffer has been read: hand it back to every CTA's FIR warps
