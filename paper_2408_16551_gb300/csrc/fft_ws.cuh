@@ -615,28 +615,23 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                     }
                                 }
                             }
+                            // the previous frame's ring slot goes back to the producer now:
+                            // every lane has used the values it loaded from it (a TMA refill
+                            // must not overtake a shared-memory read still in flight)
+                            __syncwarp();
+                            if (lane == 0 && pc > 0) mbar_arrive(empty0 + 8 * ((pc - 1) % NSLOT));
                         }
                         ++pc;
                         // ---- feed the T spectra this frame belongs to ----
                         // frame i contributes h[m] * x to spectrum i - m; slot (i - m) mod TT
 #pragma unroll
-                        for (int m = 0; m < TT; ++m) {
+                        for (int b = 0; b < NB; ++b) pend[k][b] = make_float2(h[0][b] * v[b].x, h[0][b] * v[b].y);
+#pragma unroll
+                        for (int m = 1; m < TT; ++m) {
                             const int js = ((k - m) % TT + TT) % TT;
 #pragma unroll
-                            for (int b = 0; b < NB; ++b) {
-                                if (m == 0) {
-                                    pend[js][b] = make_float2(h[0][b] * v[b].x, h[0][b] * v[b].y);
-                                } else {
-                                    pend[js][b] = fma2(make_float2(h[m][b], h[m][b]), v[b], pend[js][b]);
-                                }
-                            }
-                        }
-                        // the ring slot goes back to the producer only now that every
-                        // lane has used the values it loaded from it (a TMA refill must
-                        // not overtake a shared-memory read still in flight)
-                        if (ok) {
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+                            for (int b = 0; b < NB; ++b)
+                                pend[js][b] = fma2(make_float2(h[m][b], h[m][b]), v[b], pend[js][b]);
                         }
                         // ---- spectrum i - TT + 1 is complete ----
                         const int64_t jspec = i - (TT - 1);
@@ -656,15 +651,16 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                 // radix-4 DIF butterfly on y[t + k Q], k = 0..3
                                 float2 *ysub = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF) +
                                                brow * 4 * C::SROW + ypad<G>(t);
-                                const float2 a0 = cadd(pend[jslot][0], pend[jslot][2]);
-                                const float2 a1 = csub(pend[jslot][0], pend[jslot][2]);
-                                const float2 a2 = cadd(pend[jslot][1], pend[jslot][3]);
-                                const float2 a3 = csub(pend[jslot][1], pend[jslot][3]);
-                                ysub[0] = cadd(a0, a2);
+                                const float2 a0 = cadd2(pend[jslot][0], pend[jslot][2]);
+                                const float2 a1 = csub2(pend[jslot][0], pend[jslot][2]);
+                                const float2 a2 = cadd2(pend[jslot][1], pend[jslot][3]);
+                                const float2 a3 = csub2(pend[jslot][1], pend[jslot][3]);
+                                const float2 mi_a3 = make_float2(a3.y, -a3.x);  // -i a3
+                                ysub[0] = cadd2(a0, a2);
                                 // the twiddles w_P^(t k1) are applied by the FFT warps' first pass
-                                ysub[C::SROW] = make_float2(a1.x + a3.y, a1.y - a3.x);
-                                ysub[2 * C::SROW] = csub(a0, a2);
-                                ysub[3 * C::SROW] = make_float2(a1.x - a3.y, a1.y + a3.x);
+                                ysub[C::SROW] = cadd2(a1, mi_a3);
+                                ysub[2 * C::SROW] = csub2(a0, a2);
+                                ysub[3 * C::SROW] = csub2(a1, mi_a3);
                             } else {
                                 float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW;
 #pragma unroll

@@ -269,24 +269,22 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                                     v[j] = make_float2((float)c2.x * sc, (float)c2.y * sc);
                                 }
                             }
+                            // the previous frame's ring slot goes back to the producer now:
+                            // every lane has used the values it loaded from it (a TMA refill
+                            // must not overtake a shared-memory read still in flight)
+                            __syncwarp();
+                            if (lane == 0 && pc > 0) mbar_arrive(empty0 + 8 * ((pc - 1) % NSLOT));
                         }
                         ++pc;
                         // frame i contributes h[m] * x to spectrum i - m (register slot (i - m) mod TT)
 #pragma unroll
-                        for (int m = 0; m < TT; ++m) {
+                        for (int j = 0; j < NB; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
+#pragma unroll
+                        for (int m = 1; m < TT; ++m) {
                             const int js = ((k - m) % TT + TT) % TT;
 #pragma unroll
-                            for (int j = 0; j < NB; ++j) {
-                                if (m == 0) pend[js][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
-                                else pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
-                            }
-                        }
-                        // the ring slot goes back to the producer only now that every
-                        // lane has used the values it loaded from it (a TMA refill must
-                        // not overtake a shared-memory read still in flight)
-                        if (ok) {
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+                            for (int j = 0; j < NB; ++j)
+                                pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
                         }
                         const int64_t jspec = i - (TT - 1);
                         if (ok && jspec >= 0) {
