@@ -55,13 +55,36 @@ def peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-def source_hash() -> str:
+def source_hash(files=None) -> str:
+    """Hash of the given source files of the library (default: all of csrc/)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2408_16551_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_2408_16551_gb300", "csrc")
+    paths = sorted(os.path.join(csrc, f) for f in files) if files else sorted(glob.glob(os.path.join(csrc, "*")))
+    for f in paths:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def gpu_local_cpus(dev_index: int):
+    """CPUs local to the GPU (sysfs local_cpulist of its PCI function), or None."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev_index)
+        path = f"/sys/bus/pci/devices/{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0/local_cpulist"
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cur = os.sched_getaffinity(0)
+        cpus &= cur
+        return cpus if cpus and cpus != cur else None
+    except Exception:
+        return None
 
 
 # ---------------------------------------------------------------------------
@@ -293,7 +316,7 @@ def run_serving(pkg, n_requests, rate_hz, warm_requests, device):
             "peak_reserved_bytes": stats["peak_reserved_bytes"]}
 
 
-def run_c3(pkg, device, reps=3):
+def run_c3(pkg, device, reps=3, paths=("fft_f32", "gemm_bf16x3", "gemm_f32"), rel_err=True):
     """Configuration 3: 64 streams x 2^20 complex64, P=4096, T=16, Blackman; every
     DFT path as one batched launch over the 64 streams; rel. L2 on sampled spectra."""
     import numpy as np
@@ -309,6 +332,8 @@ def run_c3(pkg, device, reps=3):
     rows = [0, 120, 240]
     for name, path in (("fft_f32", pkg.PFB_DFT_FFT_F32), ("gemm_bf16x3", pkg.PFB_DFT_GEMM_BF16X3),
                        ("gemm_f32", pkg.PFB_DFT_GEMM_F32)):
+        if name not in paths:
+            continue
         try:
             plan = pkg.Plan(P, T, pkg.PFB_IN_C64, win, path)
             S = plan.out_spectra(xs_host[0].size)
@@ -325,8 +350,11 @@ def run_c3(pkg, device, reps=3):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / r
-            errs = [sampled_rel_l2(outs[i], xs_host[i], pkg.PFB_IN_C64, P, T, win, rows) for i in (0, 37)]
-            out[name] = {"gsps": n_total / (ms * 1e-3) / 1e9, "ms": ms, "rel_l2": max(errs), "kernel": plan.kernel_name}
+            errs = [sampled_rel_l2(outs[i], xs_host[i], pkg.PFB_IN_C64, P, T, win, rows) for i in (0, 37)] \
+                if rel_err else [None]
+            out[name] = {"gsps": n_total / (ms * 1e-3) / 1e9, "ms": ms, "rel_l2": max(errs) if rel_err else None,
+                         "kernel": plan.kernel_name, "variant": plan.variant,
+                         "hbm_frac": (n_total * 8 + len(xs) * S * P * 8) / (ms * 1e-3) / (peaks()[0] * 1e9)}
             batch.close(); plan.close()
             del outs
         except pkg.PFBError as e:
@@ -389,6 +417,8 @@ def main():
     ap.add_argument("--variant", type=int, default=-1, help="kernel variant of the headline path (-1: autotune / default)")
     ap.add_argument("--path", default="fft", choices=["fft", "bf16x3"],
                     help="DFT route of the headline step: FP32 FFT, or the split-bf16 tensor-core DFT")
+    ap.add_argument("--c3-only", action="store_true",
+                    help="time only configuration 3 (64 x 2^20, P=4096) through the --path route (profiler runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -411,6 +441,11 @@ def main():
     import paper_2408_16551_gb300 as pkg
     from paper_2408_16551_gb300 import replicas
 
+    if args.c3_only:
+        paths = ("fft_f32",) if args.path == "fft" else ("gemm_bf16x3",)
+        print(json.dumps({"c3": run_c3(pkg, device, paths=paths, rel_err=False)}), flush=True)
+        return
+
     spec, x = workload_c2()
     P, T = spec.P, spec.T
     n = int(x.size)
@@ -431,7 +466,8 @@ def main():
     # ---------------- headline: device-resident inputs -----------------
     for i in range(args.warmup):
         plan.execute(xs[i % nsets], out=outs[i % nsets], stream=stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    # two events around the K steps (events between launches would add gaps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     sampler = ClockSampler(gpu_index_for(local_rank)) if not args.minimal else None
     if sampler:
         sampler.start()
@@ -442,7 +478,7 @@ def main():
     ev[0].record(stream)
     for i in range(args.steps):
         plan.execute(xs[i % nsets], out=outs[i % nsets], stream=stream)
-        ev[i + 1].record(stream)
+    ev[1].record(stream)
     torch.cuda.synchronize()
     replicas.barrier()
     gpu_launches = pkg.launch_count() - launches0
@@ -456,21 +492,21 @@ def main():
         clocks = sampler.stop()
     else:
         clocks = None
-    total_ms = ev[0].elapsed_time(ev[-1])
-    per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[1])
     ms_step_local = total_ms / args.steps
     ms_step = replicas.max_over_ranks(ms_step_local)
     value = world * n / (ms_step * 1e-3) / 1e9
 
     hbm, bf16, bf16s, peak_kind = peaks()
     alg_bytes = n * 8 + S * P * 8
-    kern_ms = sum(per_launch) / len(per_launch)
+    kern_ms = ms_step_local  # one kernel launch per step: the average launch duration
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     traffic = None
     prof = load_json(os.path.join(ROOT, "profiles", "traffic.json"))
     kkey = f"{plan.kernel_name}:{plan.variant}"
-    if prof and prof.get("source_hash") == source_hash() and kkey in prof.get("kernels", {}):
-        traffic = prof["kernels"][kkey].get("dram_bytes_per_launch")
+    kent = (prof or {}).get("kernels", {}).get(kkey)
+    if kent and kent.get("source_hash") == source_hash(kent.get("sources")):
+        traffic = kent.get("dram_bytes_per_launch")  # counters taken on these very sources
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": f"{plan.kernel_name} variant {plan.variant}",
                 "algorithmic_bytes_per_launch": alg_bytes,
@@ -526,8 +562,16 @@ def main():
         line["paths"] = paths
 
         if not args.no_e2e:
-            hin = torch.from_numpy(x).pin_memory()
+            # pinned buffers on the GPU's local CPU node (first touch by this
+            # thread while its affinity is that node), then the old affinity back
+            local = gpu_local_cpus(gpu_index_for(local_rank))
+            old_aff = os.sched_getaffinity(0)
+            if local:
+                os.sched_setaffinity(0, local)
+            hin = torch.empty(x.shape, dtype=torch.complex64).pin_memory()
+            hin.numpy()[...] = x
             hout = torch.empty((S, P), dtype=torch.complex64).pin_memory()
+            hout.numpy()[...] = 0
             xin = hin.numpy()
             xout = hout.numpy()
             for _ in range(2):
@@ -538,8 +582,12 @@ def main():
             for _ in range(k2):
                 plan.execute_host(xin, xout)
             dt = (time.perf_counter() - t0) / k2
+            if local:
+                os.sched_setaffinity(0, old_aff)
             line["e2e"] = {"value": n / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * 8,
-                           "d2h_bytes_per_step": S * P * 8, "api": "pfb_execute_host (pinned host buffers)"}
+                           "d2h_bytes_per_step": S * P * 8, "api": "pfb_execute_host (pinned host buffers)",
+                           "host_buffers": f"pinned, first touched on the GPU-local CPUs ({len(local)} cpus)"
+                           if local else "pinned"}
 
         if not args.no_configs and rank == 0:
             del xs, outs

@@ -28,8 +28,9 @@
 //        transforms (pre-twiddles w_PL^(n' k1')), Z -> W;
 //     3. pass 2, W -> bins k = c + CS*(4m + k1') of the output rows.
 // Data hand-overs between CTAs are byte-counted on the receiver's mbarrier
-// (no release fence on the sender's side); buffer hand-backs are relaxed
-// remote arrivals, issued after the values were consumed.  Every wait is
+// (no release fence on the sender's side; the receiver's CTA-scope wait on
+// its own barrier sees the bytes); buffer hand-backs are relaxed remote
+// arrivals, issued after the values were consumed.  Every wait is
 // bounded (1 s of %globaltimer); a timeout sets the launch's error word and
 // the roles wind down; all threads of all CTAs meet at a final cluster
 // barrier, so no CTA exits while a peer may still touch its shared memory.
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                             // every CTA's cross step consumed this X buffer's previous batch
                             if (brow == 0 && bc >= 2 &&
                                 !__all_sync(0xffffffffu,
-                                            mbar_wait_cluster(xempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
+                                            mbar_wait(xempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
                                 *abort_flag = 1;
                                 ok = false;
                             }
@@ -335,14 +336,14 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                 float2 *out_rows = d.out + (sA + qb * SB) * P;
                 const int nrows = (int)min((int64_t)SB, nspec - qb * SB);
                 // every CTA's branch sums for this batch have landed in our X buffer
-                if (fail_any(mbar_wait_cluster(xfull0 + 8 * (bc & 1), (bc >> 1) & 1))) {
+                if (fail_any(mbar_wait(xfull0 + 8 * (bc & 1), (bc >> 1) & 1))) {
                     *abort_flag = 1;
                     ok = false;
                     break;
                 }
                 if (ft == 0 && bc + 2 < nbatch) mbar_expect_tx(xfull0 + 8 * (bc & 1), C::BYTES_X);  // next use
                 // every CTA finished pass 1 of the previous batch: all Z buffers are free
-                if (bc >= 1 && fail_any(mbar_wait_cluster(zempty, (bc - 1) & 1))) {
+                if (bc >= 1 && fail_any(mbar_wait(zempty, (bc - 1) & 1))) {
                     *abort_flag = 1;
                     ok = false;
                     break;
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                     for (int r = 0; r < CS; ++r) mbar_arrive_cluster_relaxed(mapa_shared(xempty0 + 8 * (bc & 1), r));
                 }
                 // ---- 2. this CTA's Z has landed: pass 1, Z -> W ----
-                if (fail_any(mbar_wait_cluster(zfull, bc & 1))) {
+                if (fail_any(mbar_wait(zfull, bc & 1))) {
                     *abort_flag = 1;
                     ok = false;
                     break;
