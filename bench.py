@@ -403,8 +403,8 @@ def run_c4(pkg, device, reps=5):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-paths", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -470,8 +470,9 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     sampler = ClockSampler(gpu_index_for(local_rank)) if not args.minimal else None
     if sampler:
+        # nvidia-smi's start-up (NVML initialisation) must be over before the timed region
         sampler.start()
-        time.sleep(0.3)
+        time.sleep(1.0)
     replicas.barrier()
     torch.cuda.synchronize()
     launches0 = pkg.launch_count()
