@@ -272,6 +272,27 @@ PFB_API pfb_status pfb_wait(pfb_server_t server, int64_t ticket, int32_t timeout
 
 PFB_API pfb_status pfb_server_get_stats(pfb_server_t server, pfb_server_stats *out_stats);
 
+/* Checkpoint of a stream's filter state (the last T-1 frames of raw input
+ * that the per-branch FIR of Sec. 5.2 carries from one chunk to the next).
+ * The blob is a 48-byte header (magic "PFBSTATE", version 1, P, T, dtype,
+ * frames taken so far, frames stored) followed by min(T-1, frames taken)
+ * frames of raw input in the plan's dtype.
+ * pfb_stream_state_size: bytes of the blob once the chunks submitted so far
+ * have run (-1 for an unknown stream).
+ * pfb_stream_state_export: waits (bounded by the server's timeout_ms) until
+ * the stream has no chunk queued or in flight, then copies the blob to
+ * host_buf (cap bytes available).  Errors: PFB_ERR_INVALID (unknown stream,
+ * cap too small, an earlier chunk failed), PFB_ERR_TIMEOUT, PFB_ERR_CUDA.
+ * pfb_stream_state_import: loads a blob into an open, idle stream of a plan
+ * with the same P, T and dtype; its next chunk then continues the exporting
+ * stream: the spectra equal those of an uninterrupted stream bit for bit.
+ * Errors: PFB_ERR_INVALID (not a blob, other P/T/dtype, truncated), as above
+ * otherwise. */
+PFB_API int64_t pfb_stream_state_size(pfb_server_t server, int64_t stream_id);
+PFB_API pfb_status pfb_stream_state_export(pfb_server_t server, int64_t stream_id, void *host_buf, int64_t cap);
+PFB_API pfb_status pfb_stream_state_import(pfb_server_t server, int64_t stream_id, const void *host_buf,
+                                           int64_t size);
+
 /* ---------------------------------------------------------------------- */
 /* Diagnostics                                                            */
 /* ---------------------------------------------------------------------- */

@@ -38,7 +38,7 @@ EXPORTED = [
     "pfb_stream_next_spectra", "pfb_submit", "pfb_poll", "pfb_wait", "pfb_server_get_stats",
     "pfb_status_string", "pfb_last_error", "pfb_launch_count", "pfb_plan_kernel_name",
     "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
-    "pfb_execute_host_noalloc",
+    "pfb_execute_host_noalloc", "pfb_stream_state_size", "pfb_stream_state_export", "pfb_stream_state_import",
 ]
 
 
@@ -101,6 +101,9 @@ def lib() -> ctypes.CDLL:
             "pfb_execute": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_execute_host": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_execute_host_noalloc": (st, [vp, vp, i64, vp, i64, vp]),
+            "pfb_stream_state_size": (i64, [vp, i64]),
+            "pfb_stream_state_export": (st, [vp, i64, vp, i64]),
+            "pfb_stream_state_import": (st, [vp, i64, vp, i64]),
             "pfb_execute_batch": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
             "pfb_batch_create": (st, [ctypes.POINTER(pfb_batch_item), i32, ctypes.POINTER(vp)]),
             "pfb_batch_launch": (st, [vp, vp]),
@@ -350,6 +353,21 @@ class Server:
 
     def wait(self, ticket: int, timeout_ms: int = 10000) -> int:
         return int(lib().pfb_wait(self.handle, ticket, timeout_ms))
+
+    def export_state(self, sid: int) -> bytes:
+        """pfb_stream_state_export: the stream's filter state as a byte blob
+        (waits until the stream's submitted chunks have run)."""
+        n = int(lib().pfb_stream_state_size(self.handle, sid))
+        if n < 0:
+            raise PFBError(PFB_ERR_INVALID, "unknown stream")
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().pfb_stream_state_export(self.handle, sid, buf, n), "pfb_stream_state_export")
+        return buf.raw
+
+    def import_state(self, sid: int, blob: bytes):
+        """pfb_stream_state_import: continue the exporting stream on stream `sid`."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().pfb_stream_state_import(self.handle, sid, buf, len(blob)), "pfb_stream_state_import")
 
     def stats(self) -> dict:
         s = pfb_server_stats()

@@ -681,3 +681,131 @@ extern "C" pfb_status pfb_server_get_stats(pfb_server_t server, pfb_server_stats
     }
     return PFB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// filter-state checkpoint: export / import of a stream's resident state
+// ---------------------------------------------------------------------------
+namespace pfb {
+
+struct StateHeader {
+    char magic[8];                 // "PFBSTATE"
+    int32_t version, P, T, in_dtype, esize, reserved;
+    int64_t frames_submitted;      // frames of all chunks the stream has taken
+    int64_t state_frames;          // frames that follow the header (<= T - 1)
+};
+static_assert(sizeof(StateHeader) == 48, "state header layout");
+
+// Wait (bounded by the server's timeout) until no submitted or in-flight work
+// of the stream remains and its last batch has finished on the device.  Called
+// with the lock held; returns with it held.
+static pfb_status wait_stream_idle(Server &s, std::unique_lock<std::mutex> &lk, PStream &ps, int64_t stream_id) {
+    const auto limit = Clock::now() + std::chrono::milliseconds((int64_t)s.desc.timeout_ms * 2 + 100);
+    auto busy = [&] {
+        if (ps.outstanding > 0) return true;
+        for (auto &b : s.batches)
+            for (Request *r : b->reqs)
+                if (r->stream_id == stream_id && !r->released) return true;
+        return false;
+    };
+    while (busy() && Clock::now() < limit) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+        lk.lock();
+    }
+    if (busy()) return fail(PFB_ERR_TIMEOUT, "stream still has work in flight");
+    if (ps.failed) return fail(PFB_ERR_INVALID, "an earlier chunk of the stream failed: its state is not defined");
+    if (ps.last_event) {
+        cudaError_t e = cudaEventSynchronize(ps.last_event);
+        if (e != cudaSuccess) return cuda_fail(e, "stream's last batch");
+    }
+    return PFB_OK;
+}
+
+static int64_t state_blob_bytes(const PStream &ps) {
+    return (int64_t)sizeof(StateHeader) + ps.state_frames * ps.plan->P * ps.plan->esize;
+}
+
+}  // namespace pfb
+
+extern "C" int64_t pfb_stream_state_size(pfb_server_t server, int64_t stream_id) {
+    if (!server) return -1;
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.streams.find(stream_id);
+    if (it == s.streams.end()) return -1;
+    // the size once the submitted chunks have run: the header and min(T - 1, frames) frames
+    const PStream &ps = *it->second;
+    const int64_t frames = std::min<int64_t>(ps.plan->T - 1, ps.frames_submitted);
+    return (int64_t)sizeof(StateHeader) + frames * ps.plan->P * ps.plan->esize;
+}
+
+extern "C" pfb_status pfb_stream_state_export(pfb_server_t server, int64_t stream_id, void *host_buf, int64_t cap) {
+    clear_error();
+    if (!server || !host_buf) return fail(PFB_ERR_INVALID, "NULL argument");
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::unique_lock<std::mutex> lk(s.mu);
+    auto it = s.streams.find(stream_id);
+    if (it == s.streams.end() || it->second->closing) return fail(PFB_ERR_INVALID, "unknown stream");
+    PStream &ps = *it->second;
+    pfb_status st = wait_stream_idle(s, lk, ps, stream_id);
+    if (st != PFB_OK) return st;
+    const int64_t need = state_blob_bytes(ps);
+    if (cap < need) return fail(PFB_ERR_INVALID, "buffer smaller than pfb_stream_state_size()");
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "PFBSTATE", 8);
+    h.version = 1;
+    h.P = ps.plan->P;
+    h.T = ps.plan->T;
+    h.in_dtype = ps.plan->in_dtype;
+    h.esize = ps.plan->esize;
+    h.frames_submitted = ps.frames_submitted;
+    h.state_frames = ps.state_frames;
+    std::memcpy(host_buf, &h, sizeof(h));
+    if (ps.state_frames > 0) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(s.device);
+        cudaError_t e = cudaMemcpy(static_cast<char *>(host_buf) + sizeof(h), ps.state[ps.cur],
+                                   (size_t)(need - (int64_t)sizeof(h)), cudaMemcpyDeviceToHost);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(e, "state export copy");
+    }
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_stream_state_import(pfb_server_t server, int64_t stream_id, const void *host_buf,
+                                              int64_t size) {
+    clear_error();
+    if (!server || !host_buf) return fail(PFB_ERR_INVALID, "NULL argument");
+    if (size < (int64_t)sizeof(StateHeader)) return fail(PFB_ERR_INVALID, "state blob shorter than its header");
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (std::memcmp(h.magic, "PFBSTATE", 8) != 0 || h.version != 1) return fail(PFB_ERR_INVALID, "not a state blob");
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::unique_lock<std::mutex> lk(s.mu);
+    auto it = s.streams.find(stream_id);
+    if (it == s.streams.end() || it->second->closing) return fail(PFB_ERR_INVALID, "unknown stream");
+    PStream &ps = *it->second;
+    const Plan &plan = *ps.plan;
+    if (h.P != plan.P || h.T != plan.T || h.in_dtype != plan.in_dtype || h.esize != plan.esize)
+        return fail(PFB_ERR_INVALID, "state blob was exported from a stream of another P, T or dtype");
+    if (h.frames_submitted < 0 || h.state_frames != std::min<int64_t>(plan.T - 1, h.frames_submitted))
+        return fail(PFB_ERR_INVALID, "inconsistent state blob");
+    const int64_t bytes = h.state_frames * plan.P * plan.esize;
+    if (size < (int64_t)sizeof(h) + bytes) return fail(PFB_ERR_INVALID, "state blob truncated");
+    pfb_status st = wait_stream_idle(s, lk, ps, stream_id);
+    if (st != PFB_OK) return st;
+    if (bytes > 0) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(s.device);
+        cudaError_t e = cudaMemcpy(ps.state[ps.cur], static_cast<const char *>(host_buf) + sizeof(h), (size_t)bytes,
+                                   cudaMemcpyHostToDevice);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(e, "state import copy");
+    }
+    ps.state_frames = h.state_frames;
+    ps.frames_submitted = h.frames_submitted;
+    return PFB_OK;
+}

@@ -196,3 +196,68 @@ def test_lost_completion_times_out(monkeypatch):
     assert res == [pkg.PFB_OK, pkg.PFB_ERR_TIMEOUT, pkg.PFB_OK]
     # the lost request still holds its slot, so destroy reports a timeout
     assert srv.close() == pkg.PFB_ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("P,T,dt,chunk,split", [(1024, 16, synth.IN_C64, 1 << 13, 3),   # state = T-1 frames
+                                                (4096, 16, synth.IN_CI8, 4096 * 4, 2),  # 8 frames < T-1
+                                                (256, 8, synth.IN_R32, 256 * 5, 0),     # exported before any chunk
+                                                (64, 4, synth.IN_C64, 64 * 2, 1)])
+def test_state_export_import_resumes_bitwise(P, T, dt, chunk, split):
+    """Checkpoint: a stream's filter state exported after `split` chunks and
+    imported into a fresh stream (on a fresh server) continues it exactly: the
+    spectra of both halves equal the uninterrupted stream bit for bit."""
+    import torch
+    nchunks = 7
+    per = 2 if dt == synth.IN_CI8 else 1
+    x = to_device(synth.small_stream(P, T, chunk * nchunks, in_dtype=dt, seed=P + split).generate())
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_HAMMING)
+    whole = plan.execute(x)
+    outs = []
+
+    def run(srv, sid, c_from, c_to):
+        tickets = []
+        for c in range(c_from, c_to):
+            S = srv.next_spectra(sid, chunk)
+            out = torch.empty((max(S, 1), P), dtype=torch.complex64, device="cuda")
+            tickets.append(srv.submit(sid, x[c * chunk * per:(c + 1) * chunk * per], chunk, out))
+            outs.append(out[:S])
+        for t in tickets:
+            assert srv.wait(t, 20000) == pkg.PFB_OK
+
+    a = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=4)
+    sa = a.open_stream(plan)
+    run(a, sa, 0, split)
+    blob = a.export_state(sa)
+    assert len(blob) == 48 + min(T - 1, split * chunk // P) * P * (8 if dt == synth.IN_C64 else (2 if dt == synth.IN_CI8 else 4))
+    a.close_stream(sa)
+    a.close()
+    b = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=4)
+    sb = b.open_stream(plan)
+    b.import_state(sb, blob)
+    run(b, sb, split, nchunks)
+    torch.cuda.synchronize()
+    got = torch.cat(outs)
+    assert got.shape == whole.shape
+    assert torch.equal(got, whole)
+    b.close_stream(sb)
+    b.close()
+
+
+def test_state_import_rejects_foreign_blobs():
+    P, T = 1024, 16
+    srv = pkg.Server(hbm_budget_bytes=1 << 32, max_slots=4)
+    p1 = pkg.Plan(P, T, pkg.PFB_IN_C64)
+    p2 = pkg.Plan(P, 8, pkg.PFB_IN_C64)
+    s1, s2 = srv.open_stream(p1), srv.open_stream(p2)
+    blob = srv.export_state(s1)
+    with pytest.raises(pkg.PFBError) as e:
+        srv.import_state(s2, blob)                     # another T
+    assert e.value.status == pkg.PFB_ERR_INVALID
+    with pytest.raises(pkg.PFBError):
+        srv.import_state(s1, b"x" * len(blob))         # not a state blob
+    with pytest.raises(pkg.PFBError):
+        srv.import_state(s1, blob[:20])                # shorter than its header
+    srv.import_state(s1, blob)                         # its own blob is fine
+    srv.close_stream(s1)
+    srv.close_stream(s2)
+    srv.close()
