@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define PFB_API_VERSION 1
+#define PFB_API_VERSION 2
 
 #if defined(__GNUC__)
 #define PFB_API __attribute__((visibility("default")))
@@ -82,12 +82,28 @@ typedef struct pfb_plan_s *pfb_plan_t;
 typedef struct pfb_batch_s *pfb_batch_t;
 typedef struct pfb_server_s *pfb_server_t;
 
+/* Order of the T taps within a branch. */
+typedef enum pfb_tap_order {
+    PFB_TAPS_CORRELATION = 0, /* y[s,p] = sum_m h[m*P+p] x[(s+m)*P+p]: the FIR-as-
+                                 convolution mapping of Sec. 4.3, O(w) = sum_n I(w+n) K(n) */
+    PFB_TAPS_CONVOLUTION = 1  /* y[s,p] = sum_m h[(T-1-m)*P+p] x[(s+m)*P+p]: the
+                                 convolution y_p(n') = sum_m h_p(m) x_p(n'-m) of the
+                                 Sec. 5.2 equation, taps reversed within each branch */
+} pfb_tap_order;
+
 /* Plan descriptor.  P: branches = channels, a power of two in [4, 4096].
  * T: taps per branch, 1..64.  in_scale: dequantisation factor for
  * PFB_IN_CI8 (must be finite; ignored for other dtypes).  user_taps_host:
  * P*T doubles (host memory, read during pfb_plan_create only) when
  * window == PFB_WIN_USER, else NULL; user taps are used as given.
- * device: CUDA ordinal, or -1 for the calling thread's current device. */
+ * device: CUDA ordinal, or -1 for the calling thread's current device.
+ * hop: samples between consecutive spectra; 0 (or P) = critically sampled.
+ * A hop D < P gives an oversampled channeliser (R = P/D spectra per frame):
+ *     X[s,k] = sum_{n<P*T} h'[n] x[s*D + n] exp(-2 pi i n k / P)
+ * (the windowed-overlap-add form of the P-hop PFB, evaluated every D
+ * samples, no phase correction), with h' the taps in tap_order.  D must
+ * divide P, R <= 32, and D * (bytes per input sample) must be a multiple of
+ * 16.  tap_order: pfb_tap_order.  reserved: must be 0. */
 typedef struct pfb_plan_desc {
     int32_t P;
     int32_t T;
@@ -97,6 +113,8 @@ typedef struct pfb_plan_desc {
     int32_t path;            /* pfb_dft_path */
     const double *user_taps_host;
     int32_t device;
+    int32_t hop;             /* 0 = P */
+    int32_t tap_order;       /* pfb_tap_order */
     int32_t reserved;        /* must be 0 */
 } pfb_plan_desc;
 
@@ -112,7 +130,8 @@ PFB_API pfb_status pfb_plan_create(const pfb_plan_desc *desc, pfb_plan_t *out_pl
 PFB_API pfb_status pfb_plan_destroy(pfb_plan_t plan);
 
 /* Spectra produced for n_samples input samples: max(0, floor(n/P) - T + 1)
- * (Sec. 5.2 valid outputs, hop P).  Returns -1 for a NULL plan or n < 0. */
+ * (Sec. 5.2 valid outputs, hop P); with a hop D < P, floor((n - P*T)/D) + 1
+ * for n >= P*T, else 0.  Returns -1 for a NULL plan or n < 0. */
 PFB_API int64_t pfb_out_spectra(pfb_plan_t plan, int64_t n_samples);
 
 /* Copy the plan's FP64 prototype filter h[0..P*T) (as generated on the GPU)

@@ -17,6 +17,10 @@ Functions and the passages they follow (TINA, arXiv 2408.16551):
 * ``dft``        -- X[s,k] = sum_p y[s,p] exp(-2 pi i (pk mod P)/P): the
   Fourier-matrix product of Sec. 4.1.
 * ``pfb``        -- ``fir`` then ``dft``.
+* ``pfb_hop``    -- the channeliser evaluated every D samples (oversampled for
+  D < P), X[s,k] = sum_{n<PT} h'[n] x[sD+n] exp(-2 pi i nk/P), with the taps
+  in the correlation order of Sec. 4.3 or reversed within each branch (the
+  convolution y_p(n') = sum_m h_p(m) x_p(n'-m) of the Sec. 5.2 equation).
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against values that
 do not come from this package.
@@ -70,6 +74,10 @@ def _load():
             lib.oracle_dft.restype = ctypes.c_int
             lib.oracle_pfb.argtypes = [d, d, i64, i64, i64, d, i64, i64, d, d, ctypes.c_int]
             lib.oracle_pfb.restype = ctypes.c_int
+            lib.oracle_num_spectra_hop.argtypes = [i64, i64, i64, i64]
+            lib.oracle_num_spectra_hop.restype = i64
+            lib.oracle_pfb_hop.argtypes = [d, d, i64, i64, i64, i64, ctypes.c_int, d, i64, i64, d, d, ctypes.c_int]
+            lib.oracle_pfb_hop.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -165,6 +173,26 @@ def pfb(x, P: int, T: int, h: np.ndarray, s0: int = 0, ns: int | None = None, th
     rc = _load().oracle_pfb(_ptr(xr), _ptr(xi), N, P, T, _ptr(h), s0, ns, _ptr(Xr), _ptr(Xi), _threads(threads))
     if rc != 0:
         raise ValueError("oracle_pfb rejected its arguments")
+    return Xr + 1j * Xi
+
+
+def num_spectra_hop(n_samples: int, P: int, T: int, D: int) -> int:
+    return int(_load().oracle_num_spectra_hop(n_samples, P, T, D))
+
+
+def pfb_hop(x, P: int, T: int, h: np.ndarray, D: int, reverse: bool = False, s0: int = 0, ns: int | None = None,
+            threads=None) -> np.ndarray:
+    """Channeliser with hop D and tap order (reverse = convolution order), X[s,k] for s in [s0, s0+ns)."""
+    xr, xi = _as_split(x)
+    N = xr.shape[0]
+    S = num_spectra_hop(N, P, T, D)
+    ns = S - s0 if ns is None else ns
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    Xr = np.zeros((max(ns, 0), P)); Xi = np.zeros((max(ns, 0), P))
+    rc = _load().oracle_pfb_hop(_ptr(xr), _ptr(xi), N, P, T, D, 1 if reverse else 0, _ptr(h), s0, ns, _ptr(Xr),
+                                _ptr(Xi), _threads(threads))
+    if rc != 0:
+        raise ValueError("oracle_pfb_hop rejected its arguments")
     return Xr + 1j * Xi
 
 

@@ -231,3 +231,75 @@ int oracle_pfb(const double *xr, const double *xi, int64_t N, int64_t P, int64_t
     free(yr); free(yi);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Oversampled channeliser and the convolution tap order                    */
+/* ------------------------------------------------------------------------ */
+
+/* Spectra of a channeliser with hop D: windows of P*T samples starting at
+ * s*D; S = floor((N - P*T)/D) + 1 for N >= P*T, else 0. */
+int64_t oracle_num_spectra_hop(int64_t N, int64_t P, int64_t T, int64_t D) {
+    if (P < 1 || T < 1 || D < 1 || N < 0) return -1;
+    if (N < P * T) return 0;
+    return (N - P * T) / D + 1;
+}
+
+typedef struct {
+    const double *xr, *xi, *h;
+    int64_t P, T, D, s0, s1, row0;
+    int reverse;
+    double *yr, *yi;
+} fir_hop_job;
+
+static void *fir_hop_worker(void *arg) {
+    fir_hop_job *j = (fir_hop_job *)arg;
+    for (int64_t s = j->s0; s < j->s1; ++s) {
+        double *orow_r = j->yr + (s - j->row0) * j->P;
+        double *orow_i = j->yi + (s - j->row0) * j->P;
+        for (int64_t p = 0; p < j->P; ++p) {
+            double ar = 0.0, ai = 0.0;
+            for (int64_t m = 0; m < j->T; ++m) {
+                /* tap m of branch p: h[m*P + p] (correlation form, Sec. 4.3) or
+                   h[(T-1-m)*P + p] (the convolution of the Sec. 5.2 equation) */
+                int64_t mt = j->reverse ? (j->T - 1 - m) : m;
+                double hv = j->h[mt * j->P + p];
+                int64_t idx = s * j->D + m * j->P + p;
+                ar += hv * j->xr[idx];
+                ai += hv * j->xi[idx];
+            }
+            orow_r[p] = ar;
+            orow_i[p] = ai;
+        }
+    }
+    return NULL;
+}
+
+/* X[s - s0, k] for s in [s0, s0+ns) of the channeliser with hop D and the
+ * given tap order: y[s,p] = sum_m h'[m*P+p] x[s*D + m*P + p], then the DFT
+ * of each row (Sec. 4.1).  D = P with reverse = 0 is oracle_pfb. */
+int oracle_pfb_hop(const double *xr, const double *xi, int64_t N, int64_t P, int64_t T, int64_t D,
+                   int reverse, const double *h, int64_t s0, int64_t ns, double *Xr, double *Xi, int nthreads) {
+    int64_t S = oracle_num_spectra_hop(N, P, T, D);
+    if (S < 0 || s0 < 0 || ns < 0 || s0 + ns > S) return -1;
+    if (ns == 0) return 0;
+    double *yr = (double *)malloc(sizeof(double) * (size_t)(ns * P));
+    double *yi = (double *)malloc(sizeof(double) * (size_t)(ns * P));
+    if (!yr || !yi) { free(yr); free(yi); return -1; }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > ns) nthreads = (int)ns;
+    fir_hop_job *jobs = (fir_hop_job *)calloc((size_t)nthreads, sizeof(fir_hop_job));
+    if (!jobs) { free(yr); free(yi); return -1; }
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].xr = xr; jobs[t].xi = xi; jobs[t].h = h;
+        jobs[t].P = P; jobs[t].T = T; jobs[t].D = D; jobs[t].reverse = reverse;
+        jobs[t].s0 = s0 + ns * t / nthreads;
+        jobs[t].s1 = s0 + ns * (t + 1) / nthreads;
+        jobs[t].row0 = s0;
+        jobs[t].yr = yr; jobs[t].yi = yi;
+    }
+    int rc = run_jobs(fir_hop_worker, jobs, sizeof(fir_hop_job), nthreads);
+    free(jobs);
+    if (rc == 0) rc = oracle_dft(yr, yi, ns, P, Xr, Xi, nthreads);
+    free(yr); free(yi);
+    return rc;
+}

@@ -29,6 +29,7 @@ PFB_ERR_TIMEOUT, PFB_ERR_INTERNAL, PFB_ERR_UNSUPPORTED = -5, -6, -7
 PFB_IN_R32, PFB_IN_C64, PFB_IN_CI8 = 0, 1, 2
 PFB_WIN_HANN, PFB_WIN_HAMMING, PFB_WIN_BLACKMAN, PFB_WIN_USER = 0, 1, 2, 3
 PFB_DFT_FFT_F32, PFB_DFT_GEMM_F32, PFB_DFT_GEMM_BF16X3 = 0, 1, 2
+PFB_TAPS_CORRELATION, PFB_TAPS_CONVOLUTION = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 << 20  # PFB_NOALLOC_SCRATCH_BYTES
 
 EXPORTED = [
@@ -46,7 +47,7 @@ class pfb_plan_desc(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("T", ctypes.c_int32), ("in_dtype", ctypes.c_int32),
                 ("in_scale", ctypes.c_float), ("window", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("user_taps_host", ctypes.POINTER(ctypes.c_double)), ("device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("hop", ctypes.c_int32), ("tap_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pfb_batch_item(ctypes.Structure):
@@ -174,10 +175,11 @@ class Plan:
     """A channeliser plan (pfb_plan_create): P branches, T taps, dtype, DFT path."""
 
     def __init__(self, P: int, T: int, in_dtype: int = PFB_IN_C64, window: int = PFB_WIN_HANN,
-                 path: int = PFB_DFT_FFT_F32, in_scale: float = 1.0, user_taps=None, device: int = -1):
+                 path: int = PFB_DFT_FFT_F32, in_scale: float = 1.0, user_taps=None, device: int = -1,
+                 hop: int = 0, tap_order: int = PFB_TAPS_CORRELATION):
         d = pfb_plan_desc()
         d.P, d.T, d.in_dtype, d.in_scale, d.window, d.path = P, T, in_dtype, in_scale, window, path
-        d.device, d.reserved = device, 0
+        d.device, d.hop, d.tap_order, d.reserved = device, hop, tap_order, 0
         self._taps_keep = None
         if user_taps is not None:
             arr = np.ascontiguousarray(user_taps, dtype=np.float64)

@@ -112,11 +112,54 @@ static pfb_status make_desc(const Plan &plan, const void *d_in, int64_t n_sample
     d.out = static_cast<float2 *>(d_out);
     d.n_state = 0;
     d.n_frames = n_samples / plan.P;
+    d.ldo = plan.P;
     d.taps = family_taps(plan);
     d.scale = plan.desc.in_scale;
     d.T = plan.T;
     return PFB_OK;
 }
+
+}  // namespace pfb
+
+pfb_status pfb::make_stream_descs(const Plan &plan, const void *d_in, int64_t n_samples, void *d_out, int64_t out_cap,
+                                  StreamDesc *descs, int *n) {
+    *n = 0;
+    if (plan.R <= 1) {
+        pfb_status st = make_desc(plan, d_in, n_samples, d_out, out_cap, descs[0]);
+        if (st == PFB_OK && descs[0].S > 0) *n = 1;
+        return st;
+    }
+    // oversampled: spectrum s = R s' + j is spectrum s' of the critically
+    // sampled PFB of the input shifted by j*hop samples (the window of spectrum
+    // s starts at s*hop = s'*P + j*hop), written to output row s
+    if (n_samples < 0) return fail(PFB_ERR_INVALID, "n_samples < 0");
+    const int64_t S = out_spectra(plan, n_samples);
+    if (S == 0) return PFB_OK;
+    if (!d_in || !d_out) return fail(PFB_ERR_INVALID, "NULL buffer with S > 0");
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(PFB_ERR_INVALID, "buffers must be 16-byte aligned");
+    if (out_cap < S) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
+    int64_t total = 0;
+    for (int j = 0; j < plan.R; ++j) {
+        const int64_t nj = n_samples - (int64_t)j * plan.hop;
+        StreamDesc &d = descs[*n];
+        std::memset(&d, 0, sizeof(d));
+        d.S = nj > 0 ? std::max<int64_t>(0, nj / plan.P - plan.T + 1) : 0;
+        if (d.S == 0) continue;
+        d.in = static_cast<const char *>(d_in) + (int64_t)j * plan.hop * plan.esize;
+        d.out = static_cast<float2 *>(d_out) + (int64_t)j * plan.P;
+        d.ldo = (int64_t)plan.R * plan.P;
+        d.n_frames = nj / plan.P;
+        d.taps = family_taps(plan);
+        d.scale = plan.desc.in_scale;
+        d.T = plan.T;
+        total += d.S;
+        ++*n;
+    }
+    if (total != S) return fail(PFB_ERR_INTERNAL, "oversampled spectra count mismatch");
+    return PFB_OK;
+}
+
+namespace pfb {
 
 struct DeviceGuard {
     int prev = -1;
@@ -157,11 +200,12 @@ extern "C" pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_s
     clear_error();
     if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
     const Plan &p = *reinterpret_cast<Plan *>(plan);
-    StreamDesc d;
-    pfb_status st = make_desc(p, d_in, n_samples, d_out, out_cap_spectra, d);
-    if (st != PFB_OK || d.S == 0) return st;
+    StreamDesc d[kMaxStreamsPerLaunch];
+    int nd = 0;
+    pfb_status st = make_stream_descs(p, d_in, n_samples, d_out, out_cap_spectra, d, &nd);
+    if (st != PFB_OK || nd == 0) return st;
     DeviceGuard g(p.device);
-    return launch_family(p, &d, 1, static_cast<cudaStream_t>(cuda_stream));
+    return launch_family(p, d, nd, static_cast<cudaStream_t>(cuda_stream));
 }
 
 extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples, void *host_out,
@@ -169,6 +213,7 @@ extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int
     clear_error();
     if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
     Plan &p = *reinterpret_cast<Plan *>(plan);
+    if (p.R > 1) return fail(PFB_ERR_UNSUPPORTED, "pfb_execute_host: oversampled plans (hop < P) run through pfb_execute");
     if (n_samples < 0) return fail(PFB_ERR_INVALID, "n_samples < 0");
     const int64_t S = out_spectra(p, n_samples);
     if (S == 0) return PFB_OK;
@@ -262,7 +307,7 @@ struct Group {
 
 static pfb_status build_groups(const pfb_batch_item *items, int32_t n, std::vector<Group> &groups, int &device) {
     if (n < 0 || (n > 0 && !items)) return fail(PFB_ERR_INVALID, "bad item list");
-    std::map<std::tuple<int, int, int, int, int>, size_t> index;
+    std::map<std::tuple<int, int, int, int, int, int>, size_t> index;
     device = -1;
     for (int i = 0; i < n; ++i) {
         const pfb_batch_item &it = items[i];
@@ -270,20 +315,21 @@ static pfb_status build_groups(const pfb_batch_item *items, int32_t n, std::vect
         const Plan &p = *reinterpret_cast<Plan *>(it.plan);
         if (device < 0) device = p.device;
         if (p.device != device) return fail(PFB_ERR_INVALID, "batch items span devices");
-        StreamDesc d;
-        pfb_status st = make_desc(p, it.d_in, it.n_samples, it.d_out, it.out_cap_spectra, d);
+        StreamDesc d[kMaxStreamsPerLaunch];
+        int nd = 0;
+        pfb_status st = make_stream_descs(p, it.d_in, it.n_samples, it.d_out, it.out_cap_spectra, d, &nd);
         if (st != PFB_OK) return fail(st, "item " + std::to_string(i) + ": " + pfb_last_error());
-        if (d.S == 0) continue;
+        if (nd == 0) continue;
         // streams share a launch when the kernel variant is the same; taps are
         // per stream (descriptor), twiddles/DFT tables depend only on P
-        auto key = std::make_tuple(p.family, p.P, p.TT, p.in_dtype, p.variant);
+        auto key = std::make_tuple(p.family, p.P, p.TT, p.in_dtype, p.variant, p.R);
         auto f = index.find(key);
         if (f == index.end()) {
             index[key] = groups.size();
             groups.push_back(Group{&p, {}});
             f = index.find(key);
         }
-        groups[f->second].descs.push_back(d);
+        for (int k = 0; k < nd; ++k) groups[f->second].descs.push_back(d[k]);
     }
     return PFB_OK;
 }

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(ClusterCfg<CS, TC>::NT, 1) k_fft_cluster(const
                 const int col = (idx % (PL / 2)) * 2;
                 if (row < nrows) {
                     const float2 x0 = Y[row * PL + col], x1 = Y[row * PL + col + 1];
-                    __stcs(reinterpret_cast<float4 *>(d.out + (s0 + row) * P + c * PL + col),
+                    __stcs(reinterpret_cast<float4 *>(d.out + (s0 + row) * d.ldo + c * PL + col),
                            make_float4(x0.x, x0.y, x1.x, x1.y));
                 }
             }

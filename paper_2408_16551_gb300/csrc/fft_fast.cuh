@@ -94,7 +94,8 @@ __device__ __forceinline__ void load_nb(const void *base, int64_t idx, float s, 
 // one Stockham pass
 // ---------------------------------------------------------------------------
 template <int P, int NB, int SB, int MR, bool PK, int PASS>
-__device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float2 *out_row0, int nrows) {
+__device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float2 *out_row0, int nrows,
+                                              int64_t ldo = P) {
     using C = FastCfg<P, NB, SB, MR>;
     constexpr int R = fft_radix(P, PASS, MR);
     constexpr int NS = fft_ns(P, PASS, MR);
@@ -169,7 +170,7 @@ __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float
             int row, j;
             rowj(q, row, j);
             if (full || row < nrows) {
-                float2 *o = out_row0 + row * P + j;
+                float2 *o = out_row0 + row * ldo + j;
 #pragma unroll
                 for (int r = 0; r < R; ++r) store_cs(o + r * NS, v[q][r]);
             }
@@ -178,9 +179,10 @@ __device__ __forceinline__ void fft_fast_pass(float2 *Y, const float2 *tw, float
 }
 
 template <int P, int NB, int SB, int MR, bool PK, int PASS>
-__device__ __forceinline__ void fft_fast_passes(float2 *Y, const float2 *tw, float2 *out_row0, int nrows) {
-    fft_fast_pass<P, NB, SB, MR, PK, PASS>(Y, tw, out_row0, nrows);
-    if constexpr (PASS + 1 < fft_npasses(P, MR)) fft_fast_passes<P, NB, SB, MR, PK, PASS + 1>(Y, tw, out_row0, nrows);
+__device__ __forceinline__ void fft_fast_passes(float2 *Y, const float2 *tw, float2 *out_row0, int nrows, int64_t ldo) {
+    fft_fast_pass<P, NB, SB, MR, PK, PASS>(Y, tw, out_row0, nrows, ldo);
+    if constexpr (PASS + 1 < fft_npasses(P, MR))
+        fft_fast_passes<P, NB, SB, MR, PK, PASS + 1>(Y, tw, out_row0, nrows, ldo);
 }
 
 // acc[j][b] += h[m][b] * v[b] for the spectra j that frame i feeds
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(P / NB, (FastCfg<P, NB, SB, MR>::MINB)) k_fft_
             for (int b = 0; b < NB; ++b) Y[j * YROW + c + b] = acc[j][b];
         __syncthreads();
         // ---- P-point FFT of the SB rows, last pass stores to HBM ----
-        fft_fast_passes<P, NB, SB, MR, PK, 0>(Y, tw, d.out + s0 * P, nrows);
+        fft_fast_passes<P, NB, SB, MR, PK, 0>(Y, tw, d.out + s0 * d.ldo, nrows, d.ldo);
     }
 }
 

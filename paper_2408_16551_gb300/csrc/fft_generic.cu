@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kGenThreads) k_fft_generic(const __grid_consta
                 const float2 x1 = cmul(in[row * P + j + half], a.tw[jj * (P / (2 * Ns))]);
                 const int base = ((j - jj) << 1) + jj;
                 if (last) {
-                    float2 *o = d.out + (s0 + row) * (int64_t)P;
+                    float2 *o = d.out + (s0 + row) * d.ldo;
                     store_cs(o + base, cadd(x0, x1));
                     store_cs(o + base + Ns, csub(x0, x1));
                 } else {

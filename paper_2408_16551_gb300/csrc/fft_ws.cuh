@@ -111,8 +111,9 @@ struct WsCfg {
 
 struct WsMeta {
     float2 *out;   // first output row of the batch
+    int64_t ldo;   // output row stride (complex64 elements)
     int nrows;
-    int pad[5];
+    int pad[3];
 };
 
 // one out-of-place Stockham pass over a batch of SB rows, run by the FFT warps
@@ -120,7 +121,7 @@ struct WsMeta {
 // k1 is first multiplied by pre[(k1 - 1) * P + n] = w_{4P}^(n k1) (k1 > 0)
 template <int P, int MR, int SB, int PASS, bool LAST, int YROW, int G, bool PRETW = false>
 __device__ __forceinline__ void ws_pass(const float2 *src, float2 *dst, const float2 *tw, float2 *out_row0, int nrows,
-                                        int ft, int nft, const float2 *pre = nullptr) {
+                                        int ft, int nft, const float2 *pre = nullptr, int64_t ldo = P) {
     constexpr int R = fft_radix(P, PASS, MR);
     constexpr int NS = fft_ns(P, PASS, MR);
     constexpr int STRIDE = P / R;
@@ -167,7 +168,7 @@ __device__ __forceinline__ void ws_pass(const float2 *src, float2 *dst, const fl
             }
         } else {
             if (row < nrows) {
-                float2 *o = out_row0 + row * P + j;
+                float2 *o = out_row0 + row * ldo + j;
 #pragma unroll
                 for (int r = 0; r < R; ++r) store_cs(o + r * NS, v[r]);
             }
@@ -177,16 +178,16 @@ __device__ __forceinline__ void ws_pass(const float2 *src, float2 *dst, const fl
 
 template <int P, int MR, int SB, int PASS, int YROW, int G>
 __device__ __forceinline__ void ws_passes(float2 *Y, float2 *W0, float2 *W1, const float2 *tw, float2 *out_row0,
-                                          int nrows, int ft, int nft, uint32_t yempty_bar, int nfftt) {
+                                          int nrows, int ft, int nft, uint32_t yempty_bar, int nfftt, int64_t ldo) {
     constexpr int NPASS = fft_npasses(P, MR);
     constexpr bool LAST = (PASS == NPASS - 1);
     const float2 *src = (PASS == 0) ? Y : ((PASS % 2 == 1) ? W0 : W1);
     float2 *dst = (PASS % 2 == 0) ? W0 : W1;
-    ws_pass<P, MR, SB, PASS, LAST, YROW, G>(src, dst, tw, out_row0, nrows, ft, nft);
+    ws_pass<P, MR, SB, PASS, LAST, YROW, G>(src, dst, tw, out_row0, nrows, ft, nft, nullptr, ldo);
     if constexpr (!LAST) {
         named_bar_sync<1>(nfftt);
         if (PASS == 0 && ft == 0) mbar_arrive(yempty_bar);  // Y has been read: the FIR warps may refill it
-        ws_passes<P, MR, SB, PASS + 1, YROW, G>(Y, W0, W1, tw, out_row0, nrows, ft, nft, yempty_bar, nfftt);
+        ws_passes<P, MR, SB, PASS + 1, YROW, G>(Y, W0, W1, tw, out_row0, nrows, ft, nft, yempty_bar, nfftt, ldo);
     } else if constexpr (PASS == 0) {
         // single-pass transform (not used for P >= 64)
         if (ft == 0) mbar_arrive(yempty_bar);
@@ -199,7 +200,7 @@ __device__ __forceinline__ void ws_passes(float2 *Y, float2 *W0, float2 *W1, con
 // instruction writes 32 consecutive bins.
 template <int Q, int SB, int SROW, int G>
 __device__ __forceinline__ void ws_dif4_last(const float2 *src, const float2 *tw, float2 *out_row0, int nrows, int ft,
-                                             int nft) {
+                                             int nft, int64_t ldo) {
     constexpr int MR = 16;
     constexpr int PASS = fft_npasses(Q, MR) - 1;
     constexpr int R = fft_radix(Q, PASS, MR);
@@ -223,7 +224,7 @@ __device__ __forceinline__ void ws_dif4_last(const float2 *src, const float2 *tw
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
         dft_reg<R, true>(v);
         if (row < nrows) {
-            float2 *o = out_row0 + row * P + 4 * j + k1;
+            float2 *o = out_row0 + row * ldo + 4 * j + k1;
 #pragma unroll
             for (int r = 0; r < R; ++r) store_cs(o + 4 * NS * r, v[r]);
         }
@@ -372,7 +373,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
             tmem_ld32(trow + kTcColD2 + 32 * h, r);
             tmem_wait_ld();
             if (q < mt.nrows) {
-                float2 *o = mt.out + q * P + lane + 32 * (16 * h);
+                float2 *o = mt.out + q * mt.ldo + lane + 32 * (16 * h);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                     store_cs(o + 32 * j, make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
             }
             const int64_t nspec = sB - sA;
             const int64_t nfr = nspec + TT - 1;
-            float2 *out_seg = d.out + sA * P;
+            float2 *out_seg = d.out + sA * d.ldo;
             int64_t first_row_spec = 0;  // segment-relative spectrum of the batch's first row
             for (int64_t i0 = 0; i0 < nfr && ok; i0 += TT) {
 #pragma unroll
@@ -669,7 +670,8 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                             ++brow;
                             if (brow == SB || jspec == nspec - 1) {
                                 if (t == 0) {
-                                    meta[bc & 1].out = out_seg + first_row_spec * P;
+                                    meta[bc & 1].out = out_seg + first_row_spec * d.ldo;
+                                    meta[bc & 1].ldo = d.ldo;
                                     meta[bc & 1].nrows = brow;
                                 }
                                 __syncwarp();
@@ -715,10 +717,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                         Yb, W, tw, nullptr, 0, ft, C::NFFTT, tw + fft_tw_entries(C::Q, C::MR));
                     named_bar_sync<1>(C::NFFTT);
                     if (ft == 0) mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
-                    ws_dif4_last<C::Q, SB, C::SROW, G>(W, tw, mt.out, mt.nrows, ft, C::NFFTT);
+                    ws_dif4_last<C::Q, SB, C::SROW, G>(W, tw, mt.out, mt.nrows, ft, C::NFFTT, mt.ldo);
                 } else {
                     ws_passes<P, C::MR, SB, 0, YROW, G>(Yb, W, W + SB * YROW, tw, mt.out, mt.nrows, ft, C::NFFTT,
-                                                        yempty0 + 8 * (bc & 1), C::NFFTT);
+                                                        yempty0 + 8 * (bc & 1), C::NFFTT, mt.ldo);
                 }
                 named_bar_sync<1>(C::NFFTT);  // W buffers free before the next batch
             }

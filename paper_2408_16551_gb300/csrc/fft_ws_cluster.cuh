@@ -103,7 +103,7 @@ __device__ __forceinline__ void st_dsmem_f2(uint32_t addr, float2 v) {
 // PL-point DFT): local bin 4m + k1' is global bin c + CS*(4m + k1').
 template <int Q, int SB, int SROW, int G, int CS>
 __device__ __forceinline__ void wc_dif4_last(const float2 *src, const float2 *tw, float2 *out_row0, int nrows,
-                                             int ft, int nft, int c) {
+                                             int ft, int nft, int c, int64_t ldo) {
     constexpr int MR = 16;
     constexpr int PASS = fft_npasses(Q, MR) - 1;
     constexpr int R = fft_radix(Q, PASS, MR);
@@ -127,7 +127,7 @@ __device__ __forceinline__ void wc_dif4_last(const float2 *src, const float2 *tw
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
         dft_reg<R, true>(v);
         if (row < nrows) {
-            float2 *o = out_row0 + row * P + c + CS * (4 * j + k1);
+            float2 *o = out_row0 + row * ldo + c + CS * (4 * j + k1);
 #pragma unroll
             for (int r = 0; r < R; ++r) store_cs(o + CS * 4 * NS * r, v[r]);
         }
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
             const int64_t nspec = sB - sA;
             const int64_t nb = (nspec + SB - 1) / SB;
             for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
-                float2 *out_rows = d.out + (sA + qb * SB) * P;
+                float2 *out_rows = d.out + (sA + qb * SB) * d.ldo;
                 const int nrows = (int)min((int64_t)SB, nspec - qb * SB);
                 // every CTA's branch sums for this batch have landed in our X buffer
                 if (fail_any(mbar_wait(xfull0 + 8 * (bc & 1), (bc >> 1) & 1))) {
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                     for (int r = 0; r < CS; ++r) mbar_arrive_cluster_relaxed(mapa_shared(zempty, r));
                 }
                 // ---- 3. pass 2, W -> bins c + CS (4m + k1') ----
-                wc_dif4_last<Q, SB, SROW, G, CS>(W, tw, out_rows, nrows, ft, NFFTT, (int)crank);
+                wc_dif4_last<Q, SB, SROW, G, CS>(W, tw, out_rows, nrows, ft, NFFTT, (int)crank, d.ldo);
                 named_bar_sync<1>(NFFTT);  // W free before the next pass 1
             }
         }

@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
                         if (ok) {
                             const int row = 32 * q + lane;
                             const int64_t s = s0 + row;
-                            float *orow = reinterpret_cast<float *>(d.out) + s * 2 * (int64_t)P + (int64_t)nt * K2_N;
+                            float *orow = reinterpret_cast<float *>(d.out) + s * 2 * d.ldo + (int64_t)nt * K2_N;
                             drain_row(trow + 128 * hb, orow + 128 * hb, s < d.S, kb == K2_CHUNK, false);
                         }
                     }
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
             if (ok) {
                 const int row = 32 * q + lane;
                 const int64_t s = s0 + row;
-                float *orow = reinterpret_cast<float *>(d.out) + s * 2 * (int64_t)P + (int64_t)nt * K2_N;
+                float *orow = reinterpret_cast<float *>(d.out) + s * 2 * d.ldo + (int64_t)nt * K2_N;
                 const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
                 drain_row(trow + 128 * hb, orow + 128 * hb, s < d.S, KBLK <= K2_CHUNK, true);
             }

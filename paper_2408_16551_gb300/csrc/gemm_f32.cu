@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__
             const int64_t s = s0 + ty + 16 * i;
             if (s < d.S) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) store_cs(d.out + s * P + k0 + tx + 16 * j, acc[i][j]);
+                for (int j = 0; j < 4; ++j) store_cs(d.out + s * d.ldo + k0 + tx + 16 * j, acc[i][j]);
             }
         }
     }

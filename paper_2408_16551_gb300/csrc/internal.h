@@ -51,6 +51,7 @@ struct StreamDesc {
     int64_t n_frames;      // total frames available (state + in)
     int64_t S;             // spectra to produce
     int64_t unit0;         // index of this stream's first work unit in the launch
+    int64_t ldo;           // output row stride in complex64 elements (P; R*P for hop P/R)
     const float *taps;     // fp32 taps, layout depends on the kernel family
     float scale;           // dequantisation factor (CI8)
     int32_t T;             // taps per branch
@@ -90,6 +91,8 @@ struct Plan {
     int family = 0;
     int esize = 0;                  // bytes per input sample
     int variant = 0;                // kernel variant (tile shape) within the family
+    int hop = 0;                    // samples between spectra (P = critically sampled)
+    int R = 1;                      // P / hop: spectra per frame (oversampling factor)
     // device tables (owned)
     double *d_h64 = nullptr;        // FP64 prototype [P*T]
     float *d_taps = nullptr;        // fp32 taps [T][P]
@@ -112,6 +115,11 @@ struct Plan {
 };
 
 int64_t out_spectra(const Plan &p, int64_t n_samples);
+// Descriptors of one stream of the plan: one, or R = P/hop interleaved
+// critically sampled ones for an oversampled plan (input shifted by j*hop,
+// output rows j, j+R, ...).  Validates the buffers; returns the count in *n.
+pfb_status make_stream_descs(const Plan &plan, const void *d_in, int64_t n_samples, void *d_out, int64_t out_cap,
+                             StreamDesc *descs, int *n);
 bool is_pow2(int64_t v);
 int ilog2(int64_t v);
 

@@ -52,6 +52,7 @@ extern "C" pfb_status pfb_execute_host_noalloc(pfb_plan_t plan, const void *host
     clear_error();
     if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
     const Plan &p = *reinterpret_cast<Plan *>(plan);
+    if (p.R > 1) return fail(PFB_ERR_UNSUPPORTED, "oversampled plans (hop < P) run through pfb_execute");
     if (n_samples < 0) return fail(PFB_ERR_INVALID, "n_samples < 0");
     const int64_t S = out_spectra(p, n_samples);
     if (S == 0) return PFB_OK;
@@ -95,6 +96,7 @@ extern "C" pfb_status pfb_execute_host_noalloc(pfb_plan_t plan, const void *host
         d.n_state = 0;
         d.n_frames = frames;
         d.S = S;
+        d.ldo = p.P;
         d.taps = family_taps(p);
         d.scale = p.desc.in_scale;
         d.T = p.T;

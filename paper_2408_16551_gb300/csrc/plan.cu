@@ -21,6 +21,10 @@ int ilog2(int64_t v) {
 
 int64_t out_spectra(const Plan &p, int64_t n_samples) {
     if (n_samples < 0) return -1;
+    if (p.R > 1) {  // hop D < P: windows start at s*D and span P*T samples
+        const int64_t L = (int64_t)p.P * p.T;
+        return n_samples < L ? 0 : (n_samples - L) / p.hop + 1;
+    }
     int64_t F = n_samples / p.P;
     int64_t S = F - p.T + 1;
     return S > 0 ? S : 0;
@@ -66,10 +70,15 @@ __global__ void normalise_kernel(double *h, int L) {
 
 // taps[m][p] = h[m*P+p] (fp32) and the zero-extended copy used by the fast
 // FFT family: pad[m][p] = h[m*P+p] for m < T, 0 for T <= m < TT.
-__global__ void taps_to_f32_kernel(const double *h, int P, int T, int TT, float *taps, float *pad) {
+// fp32 tap tables [T][P] (and the zero-extended [TT][P] copy); with the
+// convolution tap order, row m of branch p holds h[(T-1-m)*P + p]
+__global__ void taps_to_f32_kernel(const double *h, int P, int T, int TT, int reverse, float *taps, float *pad) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P * T) taps[i] = (float)h[i];
-    if (pad && i < P * TT) pad[i] = (i < P * T) ? (float)h[i] : 0.0f;
+    if (i >= P * (TT > T ? TT : T)) return;
+    const int m = i / P, p = i % P;
+    const float v = (m < T) ? (float)h[(reverse ? (T - 1 - m) : m) * P + p] : 0.0f;
+    if (i < P * T) taps[i] = v;
+    if (pad && i < P * TT) pad[i] = v;
 }
 
 // exp(-2 pi i e / M) in FP64, rounded to fp32.
@@ -123,6 +132,8 @@ pfb_status build_fft_fast_twiddles(Plan &plan) {
 // plan lifetime
 // ---------------------------------------------------------------------------
 
+static_assert(sizeof(pfb_plan_desc) == 48, "pfb_plan_desc layout (the Python binding mirrors it)");
+
 static pfb_status validate(const pfb_plan_desc *d) {
     if (!d) return fail(PFB_ERR_INVALID, "descriptor is NULL");
     if (!is_pow2(d->P) || d->P < 4 || d->P > 4096)
@@ -138,6 +149,15 @@ static pfb_status validate(const pfb_plan_desc *d) {
     if (d->in_dtype == PFB_IN_CI8 && !std::isfinite(d->in_scale))
         return fail(PFB_ERR_INVALID, "in_scale must be finite");
     if (d->reserved != 0) return fail(PFB_ERR_INVALID, "reserved field must be 0");
+    if (d->tap_order != PFB_TAPS_CORRELATION && d->tap_order != PFB_TAPS_CONVOLUTION)
+        return fail(PFB_ERR_INVALID, "bad tap_order");
+    if (d->hop != 0 && d->hop != d->P) {
+        const int esize = d->in_dtype == PFB_IN_R32 ? 4 : d->in_dtype == PFB_IN_C64 ? 8 : 2;
+        if (d->hop < 1 || d->hop > d->P || d->P % d->hop != 0) return fail(PFB_ERR_INVALID, "hop must divide P");
+        if (d->P / d->hop > kMaxStreamsPerLaunch) return fail(PFB_ERR_INVALID, "oversampling P/hop above 32");
+        if ((d->hop * esize) % 16 != 0)
+            return fail(PFB_ERR_INVALID, "hop * bytes per sample must be a multiple of 16");
+    }
     return PFB_OK;
 }
 
@@ -173,6 +193,8 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     p->in_dtype = desc->in_dtype;
     p->path = desc->path;
     p->esize = desc->in_dtype == PFB_IN_R32 ? 4 : desc->in_dtype == PFB_IN_C64 ? 8 : 2;
+    p->hop = desc->hop ? desc->hop : desc->P;
+    p->R = desc->P / p->hop;
     if (desc->path == PFB_DFT_FFT_F32) {
         p->family = fft_fast_supported(p->P, p->T)      ? FAM_FFT_FAST
                     : fft_cluster_supported(p->P, p->T) ? FAM_FFT_CLUSTER
@@ -201,7 +223,8 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     PFB_CUDA_TRY(cudaMalloc(&p->d_taps, sizeof(float) * L));
     if (padded) PFB_CUDA_TRY(cudaMalloc(&p->d_taps_pad, sizeof(float) * P * p->TT));
     int nconv = P * (p->TT > T ? p->TT : T);
-    taps_to_f32_kernel<<<(nconv + 255) / 256, 256>>>(p->d_h64, P, T, p->TT, p->d_taps, p->d_taps_pad);
+    taps_to_f32_kernel<<<(nconv + 255) / 256, 256>>>(p->d_h64, P, T, p->TT, desc->tap_order == PFB_TAPS_CONVOLUTION,
+                                                     p->d_taps, p->d_taps_pad);
     g_launches++;
 
     PFB_CUDA_TRY(cudaMalloc(&p->d_tw_r2, sizeof(float2) * (P / 2)));

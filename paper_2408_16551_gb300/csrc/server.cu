@@ -302,6 +302,7 @@ static void launch_batch(Server &s) {
             d.n_state = ps.state_frames;
             d.n_frames = n_frames;
             d.S = S;
+            d.ldo = plan.P;
             d.taps = family_taps(plan);
             d.scale = plan.desc.in_scale;
             d.T = plan.T;
@@ -496,6 +497,7 @@ extern "C" pfb_status pfb_stream_open(pfb_server_t server, pfb_plan_t plan, int6
     Server &s = *reinterpret_cast<Server *>(server);
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (p->device != s.device) return fail(PFB_ERR_INVALID, "plan is on another device");
+    if (p->R > 1) return fail(PFB_ERR_UNSUPPORTED, "streams of oversampled plans (hop < P) are not served");
     const int64_t bytes = (int64_t)std::max(p->T - 1, 1) * p->P * p->esize;
     std::lock_guard<std::mutex> lk(s.mu);
     if (s.reserved + 2 * bytes > s.desc.hbm_budget_bytes) return fail(PFB_ERR_OOM, "stream state does not fit the budget");

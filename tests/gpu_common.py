@@ -38,3 +38,10 @@ def assert_close(got, ref, tol_l2=TOL_F32, tol_max=TOL_MAX_F32, what=""):
     em = max_rel(got, ref)
     assert e2 <= tol_l2 and em <= tol_max, f"{what}: rel_l2={e2:.3e} (tol {tol_l2}) max_rel={em:.3e} (tol {tol_max})"
     return e2, em
+
+
+def reference_hop(x: np.ndarray, in_dtype: int, P: int, T: int, window: int, D: int, reverse: bool = False,
+                  scale: float = 1.0, s0: int = 0, ns=None):
+    """Oracle output of the channeliser with hop D and tap order (reverse = convolution order)."""
+    h = oracle.prototype(P, T, window)
+    return oracle.pfb_hop(oracle.dequant(x, in_dtype, scale), P, T, h, D, reverse=reverse, s0=s0, ns=ns)

@@ -57,7 +57,9 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad", [dict(P=0), dict(P=48), dict(P=8192), dict(T=0), dict(T=65), dict(in_dtype=3),
                                  dict(window=4), dict(window=3), dict(path=3), dict(reserved=1),
-                                 dict(in_dtype=2, in_scale=float("inf"))])
+                                 dict(in_dtype=2, in_scale=float("inf")), dict(hop=3), dict(hop=-2), dict(hop=65),
+                                 dict(hop=1), dict(in_dtype=2, hop=4), dict(P=4096, hop=64), dict(tap_order=2),
+                                 dict(tap_order=-1)])
 def test_plan_create_rejects_invalid_descriptors(L, bad):
     h = ctypes.c_void_p()
     st = L.pfb_plan_create(ctypes.byref(_desc(**bad)), ctypes.byref(h))
@@ -90,7 +92,7 @@ def test_server_create_rejects_invalid(L, bad):
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(pkg.pfb_plan_desc) == 40
+    assert ctypes.sizeof(pkg.pfb_plan_desc) == 48
     assert ctypes.sizeof(pkg.pfb_batch_item) == 40
     assert ctypes.sizeof(pkg.pfb_server_desc) == 24
     assert ctypes.sizeof(pkg.pfb_server_stats) == 11 * 8 + 3 * 8

@@ -351,3 +351,71 @@ def test_ws_repeatable_at_scale(variant):
     a = plan.execute(xd).clone()
     for _ in range(5):
         assert torch.equal(plan.execute(xd), a)
+
+
+HOP = [(1024, 16, synth.IN_C64, 512, 0), (1024, 16, synth.IN_C64, 256, 1), (256, 8, synth.IN_R32, 64, 0),
+       (64, 4, synth.IN_CI8, 16, 1), (4096, 16, synth.IN_C64, 2048, 0), (2048, 8, synth.IN_CI8, 512, 1),
+       (512, 16, synth.IN_C64, 128, 0), (32, 4, synth.IN_C64, 16, 1), (4096, 12, synth.IN_R32, 1024, 1)]
+
+
+@pytest.mark.parametrize("P,T,dt,D,rev", HOP)
+def test_oversampled_and_tap_order_match_oracle(P, T, dt, D, rev):
+    """Hop D < P (oversampled channeliser) and the convolution tap order, every
+    kernel variant of the plan's family, against the FP64 oracle."""
+    import torch
+    from gpu_common import reference_hop
+    S_want = 3 * (P // D) + 7
+    n = P * T + D * (S_want - 1) + D // 2 + 1      # ragged tail shorter than the hop
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=P + D + rev).generate()
+    order = pkg.PFB_TAPS_CONVOLUTION if rev else pkg.PFB_TAPS_CORRELATION
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_HAMMING, hop=D, tap_order=order)
+    assert plan.out_spectra(n) == S_want
+    ref = reference_hop(x, dt, P, T, synth.WIN_HAMMING, D, reverse=bool(rev))
+    assert ref.shape[0] == S_want
+    xd = to_device(x)
+    for v in range(plan.num_variants):
+        try:
+            plan.variant = v
+        except pkg.PFBError:
+            continue
+        X = plan.execute(xd)
+        torch.cuda.synchronize()
+        assert_close(X.cpu().numpy(), ref, what=f"hop {D} rev {rev} {plan.kernel_name} variant {v}")
+
+
+@pytest.mark.parametrize("path,P,T,D", [(pkg.PFB_DFT_GEMM_BF16X3, 1024, 16, 512), (pkg.PFB_DFT_GEMM_F32, 256, 8, 128),
+                                        (pkg.PFB_DFT_GEMM_BF16X3, 4096, 16, 2048)])
+def test_oversampled_gemm_paths(path, P, T, D):
+    import torch
+    from gpu_common import TOL_BF16X3, TOL_MAX_BF16X3, TOL_MAX_F32, reference_hop
+    n = P * T + D * 20 + 3
+    x = synth.small_stream(P, T, n, seed=D).generate()
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_BLACKMAN, path, hop=D)
+    ref = reference_hop(x, synth.IN_C64, P, T, synth.WIN_BLACKMAN, D)
+    X = plan.execute(to_device(x))
+    torch.cuda.synchronize()
+    if path == pkg.PFB_DFT_GEMM_BF16X3:
+        assert_close(X.cpu().numpy(), ref, TOL_BF16X3, TOL_MAX_BF16X3, what="bf16x3 hop")
+    else:
+        assert_close(X.cpu().numpy(), ref, TOL_F32, TOL_MAX_F32, what="gemm f32 hop")
+
+
+def test_oversampled_batch_equals_single():
+    import torch
+    P, T, D = 1024, 16, 256
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, hop=D)
+    lens = [P * T + D * 50 + 3, P * T - 1, P * T + D * 5, P * 40 + 17]
+    xs = [to_device(synth.small_stream(P, T, n, seed=90 + i).generate()) for i, n in enumerate(lens)]
+    singles = [plan.execute(x).clone() if plan.out_spectra(x.numel()) > 0 else None for x in xs]
+    outs = [torch.full((max(plan.out_spectra(x.numel()), 1), P), 5.0, dtype=torch.complex64, device="cuda")
+            for x in xs]
+    pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xs, outs)])
+    torch.cuda.synchronize()
+    for s, o in zip(singles, outs):
+        if s is not None:
+            assert torch.equal(o[:s.shape[0]], s)
+        else:
+            assert torch.all(o == 5.0)
+    with pytest.raises(pkg.PFBError) as e:
+        plan.execute_host(np.zeros(P * T * 2, dtype=np.complex64))
+    assert e.value.status == pkg.PFB_ERR_UNSUPPORTED

@@ -367,3 +367,66 @@ def test_factored_dft_model_split_error_is_bounded():
     y = (rng.standard_normal((6, 1024)) + 1j * rng.standard_normal((6, 1024))).astype(np.complex64)
     e = oracle.rel_l2(oracle.factored_dft_model(y, 32, 32), np.fft.fft(y.astype(np.complex128), axis=1))
     assert 1e-7 < e < 1e-5
+
+
+# --------------------------------------------------------------------------
+# oversampled channeliser (hop D < P) and the convolution tap order
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("P,T", [(8, 3), (16, 4), (32, 2)])
+def test_hop_P_is_the_critically_sampled_pfb(P, T):
+    rng = np.random.default_rng(P + T)
+    x = _rand_c(rng, P * (T + 9) + 3)
+    h = oracle.prototype(P, T, oracle.WIN_HAMMING)
+    assert np.array_equal(oracle.pfb_hop(x, P, T, h, P), oracle.pfb(x, P, T, h))
+
+
+@pytest.mark.parametrize("P,T,D", [(8, 3, 4), (16, 4, 2), (16, 2, 8), (32, 3, 4), (8, 1, 2)])
+def test_hop_matches_numpy_wola(P, T, D):
+    """Brute force with numpy: each spectrum is the P-point FFT of the folded
+    window h * x[sD : sD + PT] (weighted overlap-add)."""
+    rng = np.random.default_rng(3 * P + D)
+    N = P * T + D * 13 + 5
+    x = _rand_c(rng, N)
+    h = oracle.prototype(P, T, oracle.WIN_BLACKMAN)
+    S = oracle.num_spectra_hop(N, P, T, D)
+    assert S == (N - P * T) // D + 1
+    ref = np.stack([np.fft.fft((h * x[s * D:s * D + P * T]).reshape(T, P).sum(axis=0)) for s in range(S)])
+    got = oracle.pfb_hop(x, P, T, h, D)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("P,T", [(8, 4), (16, 3), (4, 5)])
+def test_convolution_order_matches_numpy_convolve(P, T):
+    """The literal Sec. 5.2 equation y_p(n') = sum_m h_p(m) x_p(n'-m) with
+    x_p(n') = x[n'P + p]: numpy.convolve per branch, valid outputs, then the FFT."""
+    rng = np.random.default_rng(P * T)
+    F = T + 11
+    x = _rand_c(rng, P * F)
+    h = oracle.prototype(P, T, oracle.WIN_HANN)
+    y = np.stack([np.convolve(x[p::P], h[p::P], mode="valid") for p in range(P)], axis=1)
+    ref = np.fft.fft(y, axis=1)
+    got = oracle.pfb_hop(x, P, T, h, P, reverse=True)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # and the oversampled convolution order is the WOLA with per-branch reversed taps
+    hr = h.reshape(T, P)[::-1].reshape(-1)
+    assert np.array_equal(oracle.pfb_hop(x, P, T, h, P // 2, reverse=True), oracle.pfb_hop(x, P, T, hr, P // 2))
+
+
+def test_hop_time_shift_and_tone_closed_form():
+    P, T, D = 16, 4, 4
+    rng = np.random.default_rng(11)
+    x = _rand_c(rng, P * T + D * 20)
+    h = oracle.prototype(P, T, oracle.WIN_HAMMING)
+    a = oracle.pfb_hop(x, P, T, h, D)
+    b = oracle.pfb_hop(x[D:], P, T, h, D)
+    assert np.array_equal(a[1:], b[:a.shape[0] - 1])
+    # a tone at channel centre c: X[s,c] = A e^{i phi} e^{2 pi i c s D / P} sum(h)
+    A, c, phi = 0.7, 5, 0.3
+    n = np.arange(P * T + D * 9)
+    xt = A * np.exp(2j * np.pi * (c * n / P + phi))
+    X = oracle.pfb_hop(xt, P, T, h, D)
+    s = np.arange(X.shape[0])
+    want = A * np.exp(2j * np.pi * phi) * np.exp(2j * np.pi * c * s * D / P) * h.sum()
+    assert np.max(np.abs(X[:, c] - want)) <= 1e-12
