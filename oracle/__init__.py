@@ -17,6 +17,10 @@ Functions and the passages they follow (TINA, arXiv 2408.16551):
 * ``dft``        -- X[s,k] = sum_p y[s,p] exp(-2 pi i (pk mod P)/P): the
   Fourier-matrix product of Sec. 4.1.
 * ``pfb``        -- ``fir`` then ``dft``.
+* ``synth``      -- the synthesis (inverse) filter bank: y~ = IDFT(X) (the
+  inverse Fourier-matrix product of Sec. 4.2, 1/P), then each branch spread
+  over the T frames it was analysed from, xh[fP+p] = sum_m h[mP+p] y~[f-m,p]
+  (the adjoint of ``fir``).
 * ``pfb_hop``    -- the channeliser evaluated every D samples (oversampled for
   D < P), X[s,k] = sum_{n<PT} h'[n] x[sD+n] exp(-2 pi i nk/P), with the taps
   in the correlation order of Sec. 4.3 or reversed within each branch (the
@@ -78,6 +82,8 @@ def _load():
             lib.oracle_num_spectra_hop.restype = i64
             lib.oracle_pfb_hop.argtypes = [d, d, i64, i64, i64, i64, ctypes.c_int, d, i64, i64, d, d, ctypes.c_int]
             lib.oracle_pfb_hop.restype = ctypes.c_int
+            lib.oracle_synth.argtypes = [d, d, i64, i64, i64, d, i64, i64, d, d]
+            lib.oracle_synth.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -194,6 +200,22 @@ def pfb_hop(x, P: int, T: int, h: np.ndarray, D: int, reverse: bool = False, s0:
     if rc != 0:
         raise ValueError("oracle_pfb_hop rejected its arguments")
     return Xr + 1j * Xi
+
+
+def synth(X: np.ndarray, P: int, T: int, h: np.ndarray, f0: int = 0, nf: int | None = None) -> np.ndarray:
+    """Synthesis filter bank: frames [f0, f0+nf) of xh (complex128, nf*P samples),
+    xh[fP+p] = sum_m h[mP+p] y~[f-m,p] with y~ = IDFT(X) (1/P) per spectrum."""
+    X = np.asarray(X, dtype=np.complex128)
+    S = X.shape[0]
+    F = S + T - 1 if S > 0 else 0
+    nf = F - f0 if nf is None else nf
+    Xr = np.ascontiguousarray(X.real); Xi = np.ascontiguousarray(X.imag)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    xr = np.zeros(max(nf, 0) * P); xi = np.zeros(max(nf, 0) * P)
+    rc = _load().oracle_synth(_ptr(Xr), _ptr(Xi), S, P, T, _ptr(h), f0, nf, _ptr(xr), _ptr(xi))
+    if rc != 0:
+        raise ValueError("oracle_synth rejected its arguments")
+    return xr + 1j * xi
 
 
 def pfb_input(x: np.ndarray, in_dtype: int, P: int, T: int, h: np.ndarray, scale: float = 1.0,

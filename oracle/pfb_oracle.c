@@ -303,3 +303,64 @@ int oracle_pfb_hop(const double *xr, const double *xi, int64_t N, int64_t P, int
     free(yr); free(yi);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Synthesis (inverse) filter bank                                          */
+/* ------------------------------------------------------------------------ */
+
+/* The adjoint of the analysis channeliser, up to the IDFT's 1/P:
+ *   y~[s,p] = (1/P) sum_{k<P} X[s,k] exp(+2 pi i (pk mod P)/P)  (the inverse
+ *             Fourier-matrix product of Sec. 4.2);
+ *   xh[f*P + p] = sum_{m<T} h[m*P + p] y~[f - m, p],  f < S + T - 1,
+ *             with y~[s,p] = 0 outside 0 <= s < S (each spectrum s spreads its
+ *             branch values over the T frames it was analysed from).
+ * Frames [f0, f0 + nf) are written to xh (nf*P complex samples). */
+int oracle_synth(const double *Xr, const double *Xi, int64_t S, int64_t P, int64_t T, const double *h,
+                 int64_t f0, int64_t nf, double *xr, double *xi) {
+    if (P < 1 || T < 1 || S < 0 || f0 < 0 || nf < 0 || f0 + nf > (S > 0 ? S + T - 1 : 0)) return -1;
+    if (nf == 0) return 0;
+    /* rows s in [f0 - T + 1, f0 + nf) intersect [0, S): their IDFTs */
+    int64_t sa = f0 - T + 1 < 0 ? 0 : f0 - T + 1;
+    int64_t sb = f0 + nf < S ? f0 + nf : S;
+    int64_t nr = sb > sa ? sb - sa : 0;
+    double *cr = (double *)malloc(sizeof(double) * (size_t)P);
+    double *ci = (double *)malloc(sizeof(double) * (size_t)P);
+    double *yr = (double *)calloc((size_t)(nr * P + 1), sizeof(double));
+    double *yi = (double *)calloc((size_t)(nr * P + 1), sizeof(double));
+    if (!cr || !ci || !yr || !yi) { free(cr); free(ci); free(yr); free(yi); return -1; }
+    for (int64_t r = 0; r < P; ++r) {
+        double a = 2.0 * ORACLE_PI * (double)r / (double)P;
+        cr[r] = cos(a);
+        ci[r] = sin(a);
+    }
+    for (int64_t s = sa; s < sb; ++s) {
+        const double *ar = Xr + s * P, *ai = Xi + s * P;
+        for (int64_t p = 0; p < P; ++p) {
+            double accr = 0.0, acci = 0.0;
+            for (int64_t k = 0; k < P; ++k) {
+                int64_t r = (p * k) % P;
+                /* (ar + i ai) * (cos + i sin) */
+                accr += ar[k] * cr[r] - ai[k] * ci[r];
+                acci += ai[k] * cr[r] + ar[k] * ci[r];
+            }
+            yr[(s - sa) * P + p] = accr / (double)P;
+            yi[(s - sa) * P + p] = acci / (double)P;
+        }
+    }
+    for (int64_t f = f0; f < f0 + nf; ++f) {
+        for (int64_t p = 0; p < P; ++p) {
+            double accr = 0.0, acci = 0.0;
+            for (int64_t m = 0; m < T; ++m) {
+                int64_t s = f - m;
+                if (s < sa || s >= sb) continue;
+                double hv = h[m * P + p];
+                accr += hv * yr[(s - sa) * P + p];
+                acci += hv * yi[(s - sa) * P + p];
+            }
+            xr[(f - f0) * P + p] = accr;
+            xi[(f - f0) * P + p] = acci;
+        }
+    }
+    free(cr); free(ci); free(yr); free(yi);
+    return 0;
+}

@@ -430,3 +430,45 @@ def test_hop_time_shift_and_tone_closed_form():
     s = np.arange(X.shape[0])
     want = A * np.exp(2j * np.pi * phi) * np.exp(2j * np.pi * c * s * D / P) * h.sum()
     assert np.max(np.abs(X[:, c] - want)) <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# synthesis (inverse) filter bank
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("P,T,S", [(8, 3, 7), (16, 4, 5), (4, 1, 6), (32, 2, 3)])
+def test_synth_is_the_adjoint_of_the_analysis(P, T, S):
+    """<A x, Y> = P <x, synth(Y)> for the analysis A of the pinned oracle, random
+    x and Y: the synthesis is A's adjoint (the IDFT carries 1/P)."""
+    rng = np.random.default_rng(7 * P + T + S)
+    N = (S + T - 1) * P
+    x = _rand_c(rng, N)
+    Y = rng.standard_normal((S, P)) + 1j * rng.standard_normal((S, P))
+    h = oracle.prototype(P, T, oracle.WIN_HAMMING)
+    lhs = np.vdot(oracle.pfb(x, P, T, h), Y)          # <A x, Y> = sum conj(Ax) Y
+    rhs = P * np.vdot(x, oracle.synth(Y, P, T, h))
+    assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs))
+
+
+def test_synth_T1_is_windowed_ifft_and_impulse_closed_form():
+    P, S = 16, 5
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((S, P)) + 1j * rng.standard_normal((S, P))
+    h = oracle.prototype(P, 1, oracle.WIN_HANN)
+    got = oracle.synth(Y, P, 1, h).reshape(S, P)
+    assert np.max(np.abs(got - h[None, :] * np.fft.ifft(Y, axis=1))) <= 1e-13
+    # one unit bin (s0, k0): frames s0..s0+T-1 carry h[mP+p] e^{2 pi i p k0 / P} / P
+    T, s0, k0 = 4, 2, 3
+    h = oracle.prototype(P, T, oracle.WIN_BLACKMAN)
+    Y = np.zeros((6, P), complex); Y[s0, k0] = 1.0
+    xh = oracle.synth(Y, P, T, h).reshape(-1, P)
+    p = np.arange(P)
+    want = np.zeros_like(xh)
+    for m in range(T):
+        want[s0 + m] = h[m * P + p] * np.exp(2j * np.pi * p * k0 / P) / P
+    assert np.max(np.abs(xh - want)) <= 1e-15
+    # frame windows: a sub-range equals the matching part of the full output
+    Yr = rng.standard_normal((6, P)) + 1j * rng.standard_normal((6, P))
+    full = oracle.synth(Yr, P, T, h)
+    assert full.size == (6 + T - 1) * P
+    assert np.array_equal(oracle.synth(Yr, P, T, h, f0=2, nf=5), full[2 * P:7 * P])
