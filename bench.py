@@ -397,6 +397,43 @@ def run_oversampled(pkg, device, xs, x_host, spec, reps=50):
     return out
 
 
+def run_synthesis(pkg, device, X_spectra, spec, reps=50):
+    """The synthesis (inverse) filter bank of the c2 analysis output: spectra
+    [16369, 1024] back to (S + T - 1) * P samples; rel. L2 on sampled frames."""
+    import numpy as np
+    import torch
+    import oracle
+    P, T = spec.P, spec.T
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_FFT_F32)
+    S = X_spectra.shape[0]
+    n_out = plan.synth_out_samples(S)
+    outs = [torch.empty((n_out,), dtype=torch.complex64, device=device) for _ in range(2)]
+    for i in range(5):
+        plan.synthesize(X_spectra, out=outs[i % 2])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(reps):
+        plan.synthesize(X_spectra, out=outs[i % 2])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    last = outs[(reps - 1) % 2]
+    h = oracle.prototype(P, T, spec.window)
+    frames = [0, 7, S // 2, S - 1, S + T - 2]
+    rows_needed = sorted({s for f in frames for s in range(max(0, f - T + 1), min(S, f + 1))})
+    Xh = np.zeros((S, P), dtype=np.complex128)
+    Xh[rows_needed] = X_spectra[rows_needed].cpu().numpy()
+    ref = np.concatenate([oracle.synth(Xh, P, T, h, f0=f, nf=1) for f in frames])
+    got = np.concatenate([last[f * P:(f + 1) * P].cpu().numpy() for f in frames])
+    alg = S * P * 8 + n_out * 8
+    out = {"workload": f"synthesis of the c2 analysis output: {S} spectra x P={P} -> {n_out} samples, T={T}",
+           "ms": ms, "gsps": n_out / (ms * 1e-3) / 1e9, "rel_l2": oracle.rel_l2(got, ref),
+           "hbm_frac": alg / (ms * 1e-3) / (peaks()[0] * 1e9), "kernel": "k_synth_ws"}
+    plan.close()
+    return out
+
+
 def run_c4(pkg, device, reps=5):
     """Configuration 4: 256 uneven streams (P in {256,512,1024,4096}, T in {8,16},
     lengths log-uniform 2^14..2^22) as one captured CUDA graph over per-variant
@@ -627,6 +664,7 @@ def main():
 
         if not args.no_configs and rank == 0:
             line["oversampled"] = run_oversampled(pkg, device, xs, x, spec)
+            line["synthesis"] = run_synthesis(pkg, device, outs[(args.steps - 1) % nsets], spec)
             del xs, outs
             torch.cuda.empty_cache()
             line["c3"] = run_c3(pkg, device)

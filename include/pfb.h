@@ -187,6 +187,20 @@ PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_
 PFB_API pfb_status pfb_execute_host_noalloc(pfb_plan_t plan, const void *host_in, int64_t n_samples,
                                             void *host_out, int64_t out_cap_spectra, void *cuda_stream);
 
+/* Synthesis (inverse) filter bank, the adjoint of pfb_execute up to the
+ * IDFT's 1/P: every spectrum X[s] goes back through the inverse DFT
+ * (Sec. 4.2, y~[s,p] = (1/P) sum_k X[s,k] exp(+2 pi i p k / P)) and each
+ * branch value is spread over the T frames it was analysed from:
+ *     xh[f*P + p] = sum_{m<T} h'[m*P + p] y~[f - m, p],  f < n_spectra + T - 1
+ * (y~ = 0 outside the given spectra; h' = the plan's taps in its tap_order).
+ * d_spectra: complex64 [n_spectra][P]; d_out: complex64 samples, at least
+ * pfb_synth_out_samples() of them.  Needs an FFT-path plan with P in {512,
+ * 1024}, T <= 16 and hop P (else PFB_ERR_UNSUPPORTED).  Asynchronous on
+ * cuda_stream.  Errors as pfb_execute. */
+PFB_API int64_t pfb_synth_out_samples(pfb_plan_t plan, int64_t n_spectra);
+PFB_API pfb_status pfb_synthesize(pfb_plan_t plan, const void *d_spectra, int64_t n_spectra, void *d_out,
+                                  int64_t out_cap_samples, void *cuda_stream);
+
 /* One stream of a batch. */
 typedef struct pfb_batch_item {
     pfb_plan_t plan;

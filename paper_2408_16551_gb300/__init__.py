@@ -40,6 +40,7 @@ EXPORTED = [
     "pfb_status_string", "pfb_last_error", "pfb_launch_count", "pfb_plan_kernel_name",
     "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
     "pfb_execute_host_noalloc", "pfb_stream_state_size", "pfb_stream_state_export", "pfb_stream_state_import",
+    "pfb_synth_out_samples", "pfb_synthesize",
 ]
 
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
             "pfb_execute_host": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_execute_host_noalloc": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_stream_state_size": (i64, [vp, i64]),
+            "pfb_synth_out_samples": (i64, [vp, i64]),
+            "pfb_synthesize": (st, [vp, vp, i64, vp, i64, vp]),
             "pfb_stream_state_export": (st, [vp, i64, vp, i64]),
             "pfb_stream_state_import": (st, [vp, i64, vp, i64]),
             "pfb_execute_batch": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
@@ -246,6 +249,23 @@ class Plan:
         _check(lib().pfb_execute(self.handle, ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                  cap, _stream_handle(stream)), "pfb_execute")
         return out[:S] if out.shape[0] != S else out
+
+    def synth_out_samples(self, n_spectra: int) -> int:
+        return int(lib().pfb_synth_out_samples(self.handle, n_spectra))
+
+    def synthesize(self, X, out=None, stream=None):
+        """pfb_synthesize: the synthesis (inverse) filter bank of complex64 spectra
+        [S, P] on the device; returns complex64 [(S + T - 1) * P] (asynchronous)."""
+        import torch
+        if X.dtype != torch.complex64 or not X.is_cuda or not X.is_contiguous() or X.dim() != 2 or X.shape[1] != self.P:
+            raise ValueError("spectra must be a contiguous complex64 CUDA tensor [S, P]")
+        S = X.shape[0]
+        n = self.synth_out_samples(S)
+        if out is None:
+            out = torch.empty((max(n, 0),), dtype=torch.complex64, device=X.device)
+        _check(lib().pfb_synthesize(self.handle, ctypes.c_void_p(X.data_ptr()), S, ctypes.c_void_p(out.data_ptr()),
+                                    out.numel(), _stream_handle(stream)), "pfb_synthesize")
+        return out[:n] if out.numel() != n else out
 
     def execute_host(self, x: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """pfb_execute_host: host buffers in and out (copies inside the call)."""
