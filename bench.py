@@ -491,6 +491,8 @@ def main():
                     help="DFT route of the headline step: FP32 FFT, or the split-bf16 tensor-core DFT")
     ap.add_argument("--c3-only", action="store_true",
                     help="time only configuration 3 (64 x 2^20, P=4096) through the --path route (profiler runs)")
+    ap.add_argument("--synth-only", action="store_true",
+                    help="time only the synthesis filter bank of the c2 analysis output (profiler runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -521,6 +523,12 @@ def main():
     spec, x = workload_c2()
     P, T = spec.P, spec.T
     n = int(x.size)
+    if args.synth_only:
+        p0 = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_FFT_F32)
+        X0 = p0.execute(torch.from_numpy(x).to(device))
+        torch.cuda.synchronize()
+        print(json.dumps({"synthesis": run_synthesis(pkg, device, X0, spec, reps=max(3, args.steps // 4))}), flush=True)
+        return
     tc_path = args.path == "bf16x3"
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_GEMM_BF16X3 if tc_path else pkg.PFB_DFT_FFT_F32)
     S = plan.out_spectra(n)
