@@ -14,10 +14,10 @@ bool ws_cluster_supported(const Plan &plan) {
     return (plan.P == 2048 || plan.P == 4096) && plan.T == plan.TT && (plan.TT == 4 || plan.TT == 8 || plan.TT == 16);
 }
 
-template <int CS, int TT, int IN>
+template <int CS, int TT, int IN, bool TC>
 static pfb_status launch_ws_cluster_k(LaunchArgs &a, cudaStream_t stream) {
-    using C = WcCfg<CS, TT, IN>;
-    auto k = k_fft_ws_cluster<CS, TT, IN>;
+    using C = WcCfg<CS, TT, IN, TC>;
+    auto k = k_fft_ws_cluster<CS, TT, IN, TC>;
     static int cap_clusters = 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -54,20 +54,20 @@ static pfb_status launch_ws_cluster_k(LaunchArgs &a, cudaStream_t stream) {
     return PFB_OK;
 }
 
-template <int CS>
+template <int CS, bool TC>
 static pfb_status launch_ws_cluster_cs(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     for (int i = 0; i < a.nstreams; ++i)
         if (a.s[i].T != plan.TT) return fail(PFB_ERR_UNSUPPORTED, "cluster variant 1 needs T in {4, 8, 16}");
     switch (plan.in_dtype * 100 + plan.TT) {
-    case PFB_IN_C64 * 100 + 4: return launch_ws_cluster_k<CS, 4, PFB_IN_C64>(a, stream);
-    case PFB_IN_C64 * 100 + 8: return launch_ws_cluster_k<CS, 8, PFB_IN_C64>(a, stream);
-    case PFB_IN_C64 * 100 + 16: return launch_ws_cluster_k<CS, 16, PFB_IN_C64>(a, stream);
-    case PFB_IN_R32 * 100 + 4: return launch_ws_cluster_k<CS, 4, PFB_IN_R32>(a, stream);
-    case PFB_IN_R32 * 100 + 8: return launch_ws_cluster_k<CS, 8, PFB_IN_R32>(a, stream);
-    case PFB_IN_R32 * 100 + 16: return launch_ws_cluster_k<CS, 16, PFB_IN_R32>(a, stream);
-    case PFB_IN_CI8 * 100 + 4: return launch_ws_cluster_k<CS, 4, PFB_IN_CI8>(a, stream);
-    case PFB_IN_CI8 * 100 + 8: return launch_ws_cluster_k<CS, 8, PFB_IN_CI8>(a, stream);
-    case PFB_IN_CI8 * 100 + 16: return launch_ws_cluster_k<CS, 16, PFB_IN_CI8>(a, stream);
+    case PFB_IN_C64 * 100 + 4: return launch_ws_cluster_k<CS, 4, PFB_IN_C64, TC>(a, stream);
+    case PFB_IN_C64 * 100 + 8: return launch_ws_cluster_k<CS, 8, PFB_IN_C64, TC>(a, stream);
+    case PFB_IN_C64 * 100 + 16: return launch_ws_cluster_k<CS, 16, PFB_IN_C64, TC>(a, stream);
+    case PFB_IN_R32 * 100 + 4: return launch_ws_cluster_k<CS, 4, PFB_IN_R32, TC>(a, stream);
+    case PFB_IN_R32 * 100 + 8: return launch_ws_cluster_k<CS, 8, PFB_IN_R32, TC>(a, stream);
+    case PFB_IN_R32 * 100 + 16: return launch_ws_cluster_k<CS, 16, PFB_IN_R32, TC>(a, stream);
+    case PFB_IN_CI8 * 100 + 4: return launch_ws_cluster_k<CS, 4, PFB_IN_CI8, TC>(a, stream);
+    case PFB_IN_CI8 * 100 + 8: return launch_ws_cluster_k<CS, 8, PFB_IN_CI8, TC>(a, stream);
+    case PFB_IN_CI8 * 100 + 16: return launch_ws_cluster_k<CS, 16, PFB_IN_CI8, TC>(a, stream);
     default: return fail(PFB_ERR_UNSUPPORTED, "cluster variant 1: no kernel for this T/dtype");
     }
 }
@@ -134,8 +134,8 @@ pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &a, cudaStream_t stre
     a.aux = plan.d_tw_r2;
     if (plan.variant == 1) {
         switch (plan.P) {
-        case 2048: return launch_ws_cluster_cs<2>(plan, a, stream);
-        case 4096: return launch_ws_cluster_cs<4>(plan, a, stream);
+        case 2048: return launch_ws_cluster_cs<2, false>(plan, a, stream);
+        case 4096: return launch_ws_cluster_cs<4, false>(plan, a, stream);
         default: return fail(PFB_ERR_UNSUPPORTED, "cluster variant 1: P must be 2048 or 4096");
         }
     }
@@ -151,6 +151,13 @@ pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &a, cudaStream_t stre
 pfb_status launch_fft_cluster_tc(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     a.aux = plan.d_tw_r2;
     a.tw = static_cast<const float2 *>(plan.d_tcf);
+    if (ws_cluster_supported(plan)) {  // warp-specialised cluster kernel, local DFT on the tensor cores
+        switch (plan.P) {
+        case 2048: return launch_ws_cluster_cs<2, true>(plan, a, stream);
+        case 4096: return launch_ws_cluster_cs<4, true>(plan, a, stream);
+        default: break;
+        }
+    }
     switch (plan.P) {
     case 2048: return launch_cluster_cs<2, true>(plan, a, stream);
     case 4096: return launch_cluster_cs<4, true>(plan, a, stream);

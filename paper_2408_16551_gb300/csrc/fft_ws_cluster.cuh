@@ -41,7 +41,7 @@
 
 namespace pfb {
 
-template <int CS, int TT, int IN>
+template <int CS, int TT, int IN, bool TC = false>
 struct WcCfg {
     static constexpr int PL = 1024;                 // branches per CTA
     static constexpr int P = CS * PL;
@@ -56,7 +56,8 @@ struct WcCfg {
     static constexpr int SB = 4;                    // spectra per batch
     static constexpr int MR = 16, G = 16;
     static constexpr int SROW = Q + Q / G + 8;      // radix-4 sub-row
-    static constexpr int ZBUF = SB * 4 * SROW;      // float2 per Z / W buffer
+    static constexpr int YROW = PL + PL / G;        // TC: natural-order Z row (padded)
+    static constexpr int ZBUF = TC ? SB * YROW : SB * 4 * SROW;  // float2 per Z (and W) buffer
     static constexpr int QC = Q / CS;               // cross-step n' per CTA
     static constexpr int NSLOT = 8;
     static constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
@@ -65,7 +66,12 @@ struct WcCfg {
     // pass list, pre-twiddles w_PL^(n' k1'), then the cross-step twiddles
     // w_P^(n k1) of this CTA's n = c*QC + nl + Q j, as [k1 - 1][j][nl]
     static constexpr int NTX = (CS - 1) * 4 * QC;
-    static constexpr int NTW = NTQ + 3 * Q + NTX;
+    static constexpr int NTW = (TC ? 0 : NTQ + 3 * Q) + NTX;
+    static constexpr int OFF_TWX = TC ? 0 : NTQ + 3 * Q;  // cross-step twiddles within the table
+    // TC (local 1024-point DFT on the tensor cores, P1 = 32): the step-2 A
+    // operand (bf16 hi and lo, K-major, 128 rows x 64), the 32-point DFT matrix
+    // in real block form (bf16 hi and lo, 64 x 64), twiddles w_1024^(k1 n2)
+    static constexpr int TC_P1 = 32, TC_LBO_A = 2064, TC_A2B = 8 * TC_LBO_A, TC_BTB = 64 * 64 * 2;
     // gather buffer X of the cross step: [s][n1][j pair][n' - c*QC], 16 bytes
     // (two branch sums, j = 2 jp and 2 jp + 1) per entry
     static constexpr int XBUF = SB * CS * 2 * QC;   // 16-byte entries per buffer
@@ -75,12 +81,18 @@ struct WcCfg {
     static constexpr int OFF_X = OFF_RING + NSLOT * FB;
     static constexpr int OFF_Z = OFF_X + 2 * XBUF * 16;
     static constexpr int OFF_W = OFF_Z + ZBUF * 8;
-    static constexpr int OFF_TW = OFF_W + ZBUF * 8;
+    static constexpr int OFF_A2 = OFF_W + (TC ? 0 : ZBUF * 8);
+    static constexpr int OFF_BT = OFF_A2 + (TC ? 2 * TC_A2B : 0);
+    static constexpr int OFF_TWT = OFF_BT + (TC ? 2 * TC_BTB : 0);
+    static constexpr int OFF_TW = OFF_TWT + (TC ? TC_P1 * TC_P1 * 8 : 0);
     static constexpr int OFF_BAR = OFF_TW + NTW * 8;
-    // full[NSLOT], empty[NSLOT], xfull[2], xempty[2], zfull, zempty
-    static constexpr int NBAR = 2 * NSLOT + 6;
+    // full[NSLOT], empty[NSLOT], xfull[2], xempty[2], zfull, zempty;
+    // TC: MMA 1 / MMA 2 complete, step-1 / step-2 operand written
+    static constexpr int NBAR = 2 * NSLOT + 6 + (TC ? 4 : 0);
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
-    static constexpr int REG_FIR = 208, REG_FFT = 72, REG_PROD = 24;
+    static constexpr int REG_FIR = TC ? 200 : 208, REG_FFT = TC ? 88 : 72, REG_PROD = 24;
+    static_assert(!TC || (OFF_A2 % 128 == 0 && OFF_BT % 128 == 0), "TC operand alignment");
+    static_assert(!TC || PL == TC_P1 * TC_P1, "TC: PL = 32 x 32, 4 spectra per 128-row tile");
     static_assert(NFT % 128 == 0 && NTHREADS % 128 == 0, "roles are whole warpgroups");
     static_assert(NFT * REG_FIR + NFFTT * REG_FFT + 128 * REG_PROD <= 65536, "register split");
     static_assert(fft_npasses(Q, MR) == 2, "two local passes after the radix-4 split");
@@ -134,10 +146,10 @@ __device__ __forceinline__ void wc_dif4_last(const float2 *src, const float2 *tw
     }
 }
 
-template <int CS, int TT, int IN>
-__global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
+template <int CS, int TT, int IN, bool TC = false>
+__global__ void __launch_bounds__(WcCfg<CS, TT, IN, TC>::NTHREADS, 1)
     k_fft_ws_cluster(const __grid_constant__ LaunchArgs a) {
-    using C = WcCfg<CS, TT, IN>;
+    using C = WcCfg<CS, TT, IN, TC>;
     constexpr int PL = C::PL, P = C::P, Q = C::Q, QC = C::QC, NB = C::NB, SB = C::SB, NSLOT = C::NSLOT;
     constexpr int SROW = C::SROW, G = C::G, NFT = C::NFT, NFFTT = C::NFFTT;
     extern __shared__ __align__(128) uint8_t wc_smem[];
@@ -148,6 +160,9 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
     float2 *tw = reinterpret_cast<float2 *>(wc_smem + C::OFF_TW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(wc_smem + C::OFF_BAR);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + C::NBAR);
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(abort_flag + 1);
+    const uint32_t mbar1 = smem_u32(&bars[2 * NSLOT + 6]), mbar2 = smem_u32(&bars[2 * NSLOT + 7]);
+    const uint32_t op1 = smem_u32(&bars[2 * NSLOT + 8]), op2 = smem_u32(&bars[2 * NSLOT + 9]);
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[NSLOT]);
     const uint32_t xfull0 = smem_u32(&bars[2 * NSLOT]), xempty0 = smem_u32(&bars[2 * NSLOT + 2]);
     const uint32_t zfull = smem_u32(&bars[2 * NSLOT + 4]), zempty = smem_u32(&bars[2 * NSLOT + 5]);
@@ -176,7 +191,13 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
             mbar_init(xempty0 + 8 * i, CS * C::NFFTW);  // every CTA's FFT warps consumed their X buffer i
         }
         mbar_init(zfull, 1);                            // own arrive + BYTES_Z from every CTA's cross step
-        mbar_init(zempty, CS * C::NFFTW);               // every CTA finished its pass 1
+        mbar_init(zempty, CS * C::NFFTW);               // every CTA finished reading its Z
+        if constexpr (TC) {
+            mbar_init(mbar1, 1);                        // MMA 1 complete (tcgen05.commit)
+            mbar_init(mbar2, 1);                        // MMA 2 complete
+            mbar_init(op1, C::NFFTT);                   // step-1 operand written (TMEM)
+            mbar_init(op2, C::NFFTT);                   // step-2 operand written (shared memory)
+        }
         mbar_init_fence();
         // arm the first use of each byte-counted barrier
         for (uint32_t i = 0; i < 2 && i < nbatch; ++i) mbar_expect_tx(xfull0 + 8 * i, C::BYTES_X);
@@ -187,7 +208,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
     // (r < P/2): the Q-point pass list, then w_PL^(n k1') = w_P^(CS n k1')
     {
         const float2 *tw_half = static_cast<const float2 *>(a.aux);
-        for (int i = threadIdx.x; i < C::NTQ; i += C::NTHREADS) {
+        for (int i = threadIdx.x; i < (TC ? 0 : C::NTQ); i += C::NTHREADS) {
             int off = 0, e = 0;
 #pragma unroll
             for (int ps = 0; ps < fft_npasses(Q, C::MR); ++ps) {
@@ -200,15 +221,26 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
             }
             tw[i] = tw_full(tw_half, e % P, P);
         }
-        for (int i = threadIdx.x; i < 3 * Q; i += C::NTHREADS)
+        for (int i = threadIdx.x; i < (TC ? 0 : 3 * Q); i += C::NTHREADS)
             tw[C::NTQ + i] = tw_full(tw_half, CS * (i % Q) * (i / Q + 1), P);
         for (int i = threadIdx.x; i < C::NTX; i += C::NTHREADS) {
             const int nl = i % QC, j = (i / QC) % 4, k1 = i / (4 * QC) + 1;
-            tw[C::NTQ + 3 * Q + i] = tw_full(tw_half, ((int)crank * QC + nl + Q * j) * k1, P);
+            tw[C::OFF_TWX + i] = tw_full(tw_half, ((int)crank * QC + nl + Q * j) * k1, P);
         }
     }
+    if constexpr (TC) {
+        // 32-point DFT-matrix tiles (hi, lo) and the twiddles w_1024^(k1 n2), 16-byte vectors
+        const int4 *src = reinterpret_cast<const int4 *>(a.tw);
+        int4 *dst = reinterpret_cast<int4 *>(wc_smem + C::OFF_BT);
+        constexpr int NV = (2 * C::TC_BTB + C::TC_P1 * C::TC_P1 * 8) / 16;
+        for (int i = threadIdx.x; i < NV; i += C::NTHREADS) dst[i] = src[i];
+        if (warp == C::NFIRW) tmem_alloc(smem_u32((const void *)tmem_slot), kTcCols);
+        fence_proxy_async_smem();  // the tables are read by the tensor core
+        tc_fence_before();
+    }
     __syncthreads();
-    cluster_sync_all();  // barriers of every CTA initialised and armed before any remote traffic
+    cluster_sync_all();
+    if constexpr (TC) tc_fence_after();  // barriers of every CTA initialised and armed before any remote traffic
 
     if (warp < C::NFIRW) {
         // ======================= FIR warps =======================
@@ -321,13 +353,44 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
         // ======================= FFT warps =======================
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::REG_FFT) : "memory");
         const int ft = threadIdx.x - NFT;
-        const float2 *twx = tw + C::NTQ + 3 * Q;  // cross-step twiddles [k1 - 1][j][nl]
+        const float2 *twx = tw + C::OFF_TWX;  // cross-step twiddles [k1 - 1][j][nl]
         const uint32_t zloc = smem_u32(Z);
         uint32_t bc = 0;
         bool ok = true;
         int si;
         int64_t sA, sB;
         auto fail_any = [&](bool w) { return named_bar_or<1>(NFFTT, !w); };
+        // TC: warp w owns spectrum q = w mod 4 of a 4-spectrum batch (TMEM lane quarter q)
+        const int q = warp & 3;
+        const uint32_t tmem = TC ? *tmem_slot : 0u;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        uint32_t ph1 = 0, ph2 = 0;  // MMA completions observed
+        auto wait_mma = [&](uint32_t bar, uint32_t &ph) {
+            const bool w = mbar_wait(bar, ph & 1);
+            ++ph;
+            const bool failed = named_bar_or<2>(NFFTT, !w);
+            tc_fence_after();
+            return !failed;
+        };
+        bool have_prev = false;
+        float2 *prev_rows = nullptr;
+        int prev_nrows = 0;
+        // TC epilogue: bins k1 + 32 k2 (k1 = lane) of spectrum q, global bin c + CS (k1 + 32 k2)
+        auto epilogue = [&](float2 *rows, int nrows, int64_t ldo) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[32];
+                tmem_ld32(trow + kTcColD2 + 32 * h, r);
+                tmem_wait_ld();
+                if (q < nrows) {
+                    float2 *o = rows + q * ldo + crank + CS * (lane + 32 * (16 * h));
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        store_cs(o + CS * 32 * j, make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])));
+                }
+            }
+        };
+        int64_t ldo_prev = 0;
         while (ok && ws_next_segment(a, range, si, sA, sB)) {
             const StreamDesc &d = a.s[si];
             const int64_t nspec = sB - sA;
@@ -374,6 +437,18 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                             for (int k1 = 1; k1 < CS; ++k1) z[k1][j] = cmul(u[k1], twx[((k1 - 1) * 4 + j) * QC + nl]);
                         }
                     }
+                    if constexpr (TC) {
+                        // natural order: Z_k1[n' + Q j] into row s of CTA k1
+#pragma unroll
+                        for (int k1 = 0; k1 < CS; ++k1) {
+                            const uint32_t zfb = mapa_shared(zf_base, k1);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                st_async_v2(mapa_shared(zloc + (uint32_t)(s * C::YROW + ypad<G>(np + Q * j)) * 8u, k1),
+                                            z[k1][j], zfb);
+                        }
+                        continue;
+                    }
                     const uint32_t zoff = (uint32_t)(4 * s * SROW + ypad<G>(np)) * 8u;
 #pragma unroll
                     for (int k1 = 0; k1 < CS; ++k1) {
@@ -402,6 +477,74 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                     break;
                 }
                 if (ft == 0 && bc + 1 < nbatch) mbar_expect_tx(zfull, C::BYTES_Z);  // next batch
+                if constexpr (TC) {
+                    // ---- 2. MMA 1 operand: row (q, n2 = lane), K = (n1, re/im), into TMEM ----
+                    const float2 *zrow = Z + q * C::YROW;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t vh[16], vl[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) split_bf16x2(zrow[ypad<G>(32 * (16 * h + j) + lane)], vh[j], vl[j]);
+                        tmem_st<16>(trow + kTcColA1 + 16 * h, vh);
+                        tmem_st<16>(trow + kTcColA1 + 32 + 16 * h, vl);
+                    }
+                    tmem_wait_st();
+                    // Z read: every CTA may send its next batch
+                    __syncwarp();
+                    if (lane == 0) {
+#pragma unroll
+                        for (int r = 0; r < CS; ++r) mbar_arrive_cluster_relaxed(mapa_shared(zempty, r));
+                    }
+                    tc_fence_before();
+                    mbar_arrive(op1);
+                    // ---- while MMA 1 runs: the previous batch's bins ----
+                    if (have_prev) {
+                        if (!wait_mma(mbar2, ph2)) {
+                            *abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        epilogue(prev_rows, prev_nrows, ldo_prev);
+                        have_prev = false;
+                    }
+                    if (!wait_mma(mbar1, ph1)) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    // ---- 3. twiddle w_1024^(n2 k1), split, transposed store: MMA 2 operand ----
+                    uint8_t *a2 = wc_smem + C::OFF_A2;
+                    const float2 *twt = reinterpret_cast<const float2 *>(wc_smem + C::OFF_TWT);
+                    const int a2_base = (lane >> 2) * C::TC_LBO_A + (lane & 3) * 4 + (4 * q) * 128;
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {  // 8 k1 per TMEM load
+                        float2 w8[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) w8[j] = twt[(8 * h + j) * C::TC_P1 + lane];
+                        uint32_t r[16];
+                        tmem_ld16(trow + kTcColD1 + 16 * h, r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int k1 = 8 * h + j;
+                            const float2 zz =
+                                cmul(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])), w8[j]);
+                            uint32_t hi, lo;
+                            split_bf16x2(zz, hi, lo);
+                            const int off = a2_base + (k1 >> 3) * 128 + (k1 & 7) * 16;
+                            *reinterpret_cast<uint32_t *>(a2 + off) = hi;
+                            *reinterpret_cast<uint32_t *>(a2 + C::TC_A2B + off) = lo;
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(op2);
+                    prev_rows = out_rows;
+                    prev_nrows = nrows;
+                    ldo_prev = d.ldo;
+                    have_prev = true;
+                    continue;
+                }
                 ws_pass<Q, C::MR, 4 * SB, 0, false, SROW, G, true>(Z, W, tw, nullptr, 0, ft, NFFTT, tw + C::NTQ);
                 named_bar_sync<1>(NFFTT);
                 if (lane == 0) {
@@ -413,9 +556,19 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
                 named_bar_sync<1>(NFFTT);  // W free before the next pass 1
             }
         }
+        if constexpr (TC) {
+            if (ok && have_prev) {
+                if (wait_mma(mbar2, ph2)) epilogue(prev_rows, prev_nrows, ldo_prev);
+                else *abort_flag = 1;
+            }
+        }
     } else {
         // ======================= producer warp(group) =======================
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::REG_PROD) : "memory");
+        if constexpr (TC) {
+            if (warp == C::PRODW + 1 && lane == 0)
+                ws_tc_mma_thread<C>(a, range, wc_smem, op1, op2, mbar1, mbar2, *tmem_slot, abort_flag);
+        }
         if (warp == C::PRODW && lane == 0) {
             uint32_t pc = 0;
             bool ok = true;
@@ -449,7 +602,14 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN>::NTHREADS, 1)
     }
     // no CTA leaves while a peer may still store into its X or Z buffers or
     // arrive on its barriers
+    if constexpr (TC) tc_fence_before();
     cluster_sync_all();
+    if constexpr (TC) {
+        if (warp == C::NFIRW) {
+            tc_fence_after();
+            tmem_dealloc(*tmem_slot, kTcCols);
+        }
+    }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
 }
 

@@ -62,7 +62,7 @@ constexpr uint32_t K2_IDESC = tc_idesc_bf16(K2_M, K2_N);
 int64_t cluster_units(int64_t S);
 
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) {
-    if (plan.variant == 1) return plan.P == 1024 ? S : cluster_units(S);
+    if (plan.variant == 1) return (plan.P == 1024 || ws_cluster_supported(plan)) ? S : cluster_units(S);
     return ((S + K2_M - 1) / K2_M) * (plan.P / (K2_N / 2));
 }
 

@@ -232,3 +232,21 @@ def test_gemm_bf16x3_factored_c3_sample():
         xin = oracle.dequant(xs_host[i], oracle.IN_C64)
         ref = np.stack([oracle.dft(oracle.fir(xin, P, T, h, s0=r, ns=1))[0] for r in rows])
         assert oracle.rel_l2(outs[i][rows].cpu().numpy(), ref) < TOL_BF16X3
+
+
+@pytest.mark.parametrize("P,T,dt,rows", [(4096, 16, synth.IN_C64, 1001), (2048, 4, synth.IN_CI8, 301),
+                                         (4096, 8, synth.IN_R32, 37)])
+def test_gemm_bf16x3_ws_cluster_repeatable_and_matches_split_model(P, T, dt, rows):
+    """The warp-specialised cluster kernel with its local DFT on the tensor cores:
+    against the oracle, and bitwise repeatable over several runs at scale."""
+    import torch
+    n = P * (T - 1 + rows) + 3
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=P * T + rows).generate()
+    plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_BLACKMAN, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan.variant == 1
+    xd = to_device(x)
+    first = plan.execute(xd).clone()
+    for _ in range(3):
+        assert torch.equal(plan.execute(xd), first)
+    ref = reference(x, dt, P, T, synth.WIN_BLACKMAN)
+    assert_close(first.cpu().numpy(), ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"ws cluster tc P={P} T={T}")
