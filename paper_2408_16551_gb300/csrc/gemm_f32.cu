@@ -7,21 +7,23 @@
 //   B = W[p, k] = exp(-2 pi i (p k mod P) / P)   (complex64, built in FP64)
 //   X[s, k] = sum_p A[s, p] B[p, k]               (complex FMA, FP32 accumulation)
 //
-// Tiling: a work unit is a 64-spectrum x 64-bin output tile; 256 threads,
-// each accumulating a 4 x 4 complex micro-tile (rows ty + 16 i, bins tx + 16 j,
+// Tiling: a work unit is a 64-spectrum x BN-bin output tile (BN = 128, or 64
+// for P = 64); 256 threads, each accumulating a 4 x BN/16 complex micro-tile (rows ty + 16 i, bins tx + 16 j,
 // conflict-free shared reads, coalesced stores).  The K loop walks 16 branches
-// at a time: the FIR computes the 64 x 16 slice of A, the matching 16 x 64
-// slice of W comes from HBM/L2.  Units are dealt round-robin so CTAs running
-// at the same time share M-tiles (input rows) and W stays hot in L2.
+// at a time: the FIR computes the 64 x 16 slice of A (taps unrolled by 4, so
+// four loads are in flight per element), the matching 16 x BN slice of W
+// comes from HBM/L2.  Units are dealt round-robin so CTAs running at the same
+// time share M-tiles (input rows) and W stays hot in L2.
 #include "devutil.cuh"
 #include "internal.h"
 
 namespace pfb {
 
-constexpr int G3_BM = 64, G3_BN = 64, G3_BK = 16, G3_THREADS = 256;
+constexpr int G3_BM = 64, G3_BK = 16, G3_THREADS = 256;
+static int g3_bn(int P) { return P >= 128 ? 128 : 64; }
 
 int64_t gemm_f32_units(const Plan &plan, int64_t S) {
-    return ((S + G3_BM - 1) / G3_BM) * (plan.P / G3_BN);
+    return ((S + G3_BM - 1) / G3_BM) * (plan.P / g3_bn(plan.P));
 }
 
 // W[p][k] = exp(-2 pi i (p k mod P) / P) in FP64, rounded to complex64
@@ -35,9 +37,10 @@ __global__ void gen_dft_f32_kernel(float2 *W, int P) {
     W[i] = make_float2((float)c, (float)-s);
 }
 
-template <int IN>
+template <int IN, int G3_BN>
 __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__ LaunchArgs a, int P) {
     using L = Loader<IN>;
+    constexpr int G3_NJ = G3_BN / 16;  // bins per thread
     __shared__ float2 As[G3_BK][G3_BM + 1];
     __shared__ float2 Bs[G3_BK][G3_BN];
     const float2 *W = static_cast<const float2 *>(a.aux);
@@ -49,11 +52,11 @@ __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__
         const int64_t lu = u - d.unit0;
         const int64_t s0 = (lu / NT) * G3_BM;
         const int k0 = (int)(lu % NT) * G3_BN;
-        float2 acc[4][4];
+        float2 acc[4][G3_NJ];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < G3_NJ; ++j) acc[i][j] = make_float2(0.f, 0.f);
         for (int pc = 0; pc < P; pc += G3_BK) {
             __syncthreads();
             // A slice: FIR of 64 spectra x 16 branches (4 per thread)
@@ -65,6 +68,7 @@ __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__
                 const int p = pc + kk;
                 float2 y = make_float2(0.f, 0.f);
                 if (s < d.S) {
+#pragma unroll 4
                     for (int m = 0; m < d.T; ++m) {
                         int64_t smp;
                         const void *src = frame_source(d, s + m, P, smp);
@@ -76,25 +80,25 @@ __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__
                 }
                 As[kk][r] = y;
             }
-            // B slice: 16 x 64 of W
+            // B slice: 16 x 128 of W
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < G3_BK * G3_BN / G3_THREADS; ++e) {
                 const int idx = t + e * G3_THREADS;
-                const int kk = idx >> 6, c = idx & 63;
+                const int kk = idx / G3_BN, c = idx % G3_BN;
                 Bs[kk][c] = __ldg(W + (int64_t)(pc + kk) * P + k0 + c);
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < G3_BK; ++kk) {
-                float2 av[4], bv[4];
+                float2 av[4], bv[G3_NJ];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+                for (int j = 0; j < G3_NJ; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < G3_NJ; ++j) {
                         acc[i][j].x = fmaf(av[i].x, bv[j].x, acc[i][j].x);
                         acc[i][j].x = fmaf(-av[i].y, bv[j].y, acc[i][j].x);
                         acc[i][j].y = fmaf(av[i].x, bv[j].y, acc[i][j].y);
@@ -107,15 +111,15 @@ __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__
             const int64_t s = s0 + ty + 16 * i;
             if (s < d.S) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) store_cs(d.out + s * d.ldo + k0 + tx + 16 * j, acc[i][j]);
+                for (int j = 0; j < G3_NJ; ++j) store_cs(d.out + s * d.ldo + k0 + tx + 16 * j, acc[i][j]);
             }
         }
     }
 }
 
-template <int IN>
+template <int IN, int BN>
 static pfb_status launch_g3(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
-    auto k = k_gemm_f32<IN>;
+    auto k = k_gemm_f32<IN, BN>;
     static int grid_cap = 0;
     if (grid_cap == 0) {
         int dev = 0, sms = 0, per_sm = 0;
@@ -136,11 +140,12 @@ static pfb_status launch_g3(const Plan &plan, LaunchArgs &a, cudaStream_t stream
 }
 
 pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
-    if (plan.P < G3_BN) return fail(PFB_ERR_UNSUPPORTED, "FP32 DFT-GEMM path needs P >= 64");
+    if (plan.P < 64) return fail(PFB_ERR_UNSUPPORTED, "FP32 DFT-GEMM path needs P >= 64");
+    const bool wide = g3_bn(plan.P) == 128;
     switch (plan.in_dtype) {
-    case PFB_IN_C64: return launch_g3<PFB_IN_C64>(plan, a, stream);
-    case PFB_IN_R32: return launch_g3<PFB_IN_R32>(plan, a, stream);
-    case PFB_IN_CI8: return launch_g3<PFB_IN_CI8>(plan, a, stream);
+    case PFB_IN_C64: return wide ? launch_g3<PFB_IN_C64, 128>(plan, a, stream) : launch_g3<PFB_IN_C64, 64>(plan, a, stream);
+    case PFB_IN_R32: return wide ? launch_g3<PFB_IN_R32, 128>(plan, a, stream) : launch_g3<PFB_IN_R32, 64>(plan, a, stream);
+    case PFB_IN_CI8: return wide ? launch_g3<PFB_IN_CI8, 128>(plan, a, stream) : launch_g3<PFB_IN_CI8, 64>(plan, a, stream);
     default: return fail(PFB_ERR_INVALID, "bad dtype");
     }
 }
