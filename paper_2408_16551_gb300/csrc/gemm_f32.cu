@@ -10,8 +10,8 @@
 // Tiling: a work unit is a 64-spectrum x BN-bin output tile (BN = 128, or 64
 // for P = 64); 256 threads, each accumulating a 4 x BN/16 complex micro-tile (rows ty + 16 i, bins tx + 16 j,
 // conflict-free shared reads, coalesced stores).  The K loop walks 16 branches
-// at a time: the FIR computes the 64 x 16 slice of A (taps unrolled by 4, so
-// four loads are in flight per element), the matching 16 x BN slice of W
+// at a time: the FIR computes the 64 x 16 slice of A (four spectra per thread:
+// each input frame is loaded once per thread), the matching 16 x BN slice of W
 // comes from HBM/L2.  Units are dealt round-robin so CTAs running at the same
 // time share M-tiles (input rows) and W stays hot in L2.
 #include "devutil.cuh"
@@ -59,26 +59,39 @@ __global__ void __launch_bounds__(G3_THREADS) k_gemm_f32(const __grid_constant__
             for (int j = 0; j < G3_NJ; ++j) acc[i][j] = make_float2(0.f, 0.f);
         for (int pc = 0; pc < P; pc += G3_BK) {
             __syncthreads();
-            // A slice: FIR of 64 spectra x 16 branches (4 per thread)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int idx = t + e * G3_THREADS;
-                const int r = idx >> 4, kk = idx & 15;
-                const int64_t s = s0 + r;
+            // A slice: FIR of 64 spectra x 16 branches.  Thread (kk, g) computes
+            // spectra 4g .. 4g+3 of branch pc + kk: it streams the T + 3 frames they
+            // share once, keeping the last four taps in registers (tap i meets
+            // spectrum 4g + r at frame 4g + r + i)
+            {
+                const int kk = t & 15, g = t >> 4;
                 const int p = pc + kk;
-                float2 y = make_float2(0.f, 0.f);
-                if (s < d.S) {
-#pragma unroll 4
-                    for (int m = 0; m < d.T; ++m) {
-                        int64_t smp;
-                        const void *src = frame_source(d, s + m, P, smp);
-                        const float2 v = L::load1(src, smp + p, d.scale);
-                        const float h = __ldg(d.taps + m * P + p);
-                        y.x = fmaf(h, v.x, y.x);
-                        y.y = fmaf(h, v.y, y.y);
+                const int64_t sg = s0 + 4 * g;
+                float2 y0 = make_float2(0.f, 0.f), y1 = y0, y2 = y0, y3 = y0;
+                float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
+                if (sg < d.S) {
+#pragma unroll 2
+                    for (int i = 0; i < d.T + 3; ++i) {
+                        h3 = h2; h2 = h1; h1 = h0;
+                        h0 = i < d.T ? __ldg(d.taps + i * P + p) : 0.f;
+                        const int64_t f = sg + i;
+                        float2 v = make_float2(0.f, 0.f);
+                        if (f < d.n_frames) {
+                            int64_t smp;
+                            const void *src = frame_source(d, f, P, smp);
+                            v = L::load1(src, smp + p, d.scale);
+                        }
+                        // frame sg + i: tap i of spectrum sg, tap i-1 of sg+1, ...
+                        y0.x = fmaf(h0, v.x, y0.x); y0.y = fmaf(h0, v.y, y0.y);
+                        y1.x = fmaf(h1, v.x, y1.x); y1.y = fmaf(h1, v.y, y1.y);
+                        y2.x = fmaf(h2, v.x, y2.x); y2.y = fmaf(h2, v.y, y2.y);
+                        y3.x = fmaf(h3, v.x, y3.x); y3.y = fmaf(h3, v.y, y3.y);
                     }
                 }
-                As[kk][r] = y;
+                As[kk][4 * g] = y0;
+                As[kk][4 * g + 1] = sg + 1 < d.S ? y1 : make_float2(0.f, 0.f);
+                As[kk][4 * g + 2] = sg + 2 < d.S ? y2 : make_float2(0.f, 0.f);
+                As[kk][4 * g + 3] = sg + 3 < d.S ? y3 : make_float2(0.f, 0.f);
             }
             // B slice: 16 x 128 of W
 #pragma unroll
