@@ -192,6 +192,7 @@ class Plan:
         _check(lib().pfb_plan_create(ctypes.byref(d), ctypes.byref(h)), "pfb_plan_create")
         self.handle = h
         self.P, self.T, self.in_dtype, self.window, self.path = P, T, in_dtype, window, path
+        self.hop = hop if hop else P   # samples between consecutive spectra
 
     def close(self):
         if getattr(self, "handle", None):

@@ -63,3 +63,115 @@ def test_shard_range_edge_cases():
     with pytest.raises(ValueError):
         replicas.shard_range(5, 3, 3)
     assert replicas.max_over_ranks(3.0) == 3.0            # no process group: identity
+
+
+# ---- stream-sharded launchers: the host logic, with the oracle doing the arithmetic ----
+
+def test_shard_streams_deal():
+    """Every stream goes to exactly one rank, the deal is the same on every rank,
+    and the loads differ by at most the largest stream."""
+    from paper_2408_16551_gb300 import synth
+    work = [s.n_samples for s in synth.config_c4(256)]
+    for world in (1, 2, 3, 4, 8):
+        deals = [replicas.shard_streams(work, r, world) for r in range(world)]
+        owned = sorted(i for d in deals for i in d)
+        assert owned == list(range(len(work)))
+        assert all(d == sorted(d) for d in deals)
+        loads = [sum(work[i] for i in d) for d in deals]
+        assert max(loads) - min(loads) <= max(work)
+        assert deals == [replicas.shard_streams(work, r, world) for r in range(world)]
+    assert replicas.shard_streams([], 0, 2) == []
+    assert replicas.shard_streams([5], 1, 2) == []          # more ranks than streams: idle rank
+    with pytest.raises(ValueError):
+        replicas.shard_streams([1, -1], 0, 2)
+    with pytest.raises(ValueError):
+        replicas.shard_streams([1], 2, 2)
+
+
+@pytest.mark.parametrize("S,T,P,hop,granule", [(241, 16, 4096, 4096, 1), (1021, 4, 16, 16, 1),
+                                               (1000, 8, 64, 32, 1), (37, 3, 4, 4, 2), (0, 4, 16, 16, 1),
+                                               (5, 16, 256, 128, 4)])
+def test_shard_stream_spectra_cover(S, T, P, hop, granule):
+    """Shares tile [0, S) in order, start on granule multiples, and each sample
+    range is exactly the span of its spectra's windows."""
+    for world in (1, 2, 3, 7):
+        nxt = 0
+        for r in range(world):
+            s0, s1, a, b = replicas.shard_stream_spectra(S, T, P, r, world, hop=hop, granule=granule)
+            assert s0 == nxt and s1 >= s0
+            assert s0 % granule == 0 or s0 == S
+            if s1 > s0:
+                assert a == s0 * hop and b == (s1 - 1) * hop + P * T
+            else:
+                assert a == b
+            nxt = s1
+        assert nxt == S
+
+
+@pytest.mark.parametrize("P,T,hop,world", [(16, 4, 16, 3), (8, 5, 8, 2), (32, 3, 8, 4)])
+def test_sharded_stream_halo_oracle(P, T, hop, world):
+    """The shards' spectra, each computed from its own input slice (halo
+    included), equal the whole stream's spectra bit for bit (FP64 oracle,
+    same arithmetic per spectrum)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(P * 100 + T)
+    N = P * 61 + 5                                          # ragged tail
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    h = oracle.prototype(P, T)
+    whole = oracle.pfb_hop(x, P, T, h, hop)
+    S = whole.shape[0]
+    parts = []
+    for r in range(world):
+        s0, s1, a, b = replicas.shard_stream_spectra(S, T, P, r, world, hop=hop)
+        if s1 > s0:
+            part = oracle.pfb_hop(x[a:b], P, T, h, hop)
+            assert part.shape[0] == s1 - s0
+            parts.append(part)
+    assert np.array_equal(np.concatenate(parts), whole)
+
+
+def _shard_worker(rank, world, port, q):
+    import numpy as np
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        P, T = 16, 4
+        rng = np.random.default_rng(11)                     # same input on every rank
+        N = P * 200
+        x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        h = oracle.prototype(P, T)
+        S = oracle.num_spectra(N, P, T)
+        s0, s1, a, b = replicas.shard_stream_spectra(S, T, P, rank, world)
+        mine = oracle.pfb(x[a:b], P, T, h) if s1 > s0 else np.zeros((0, P), complex)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (s0, s1, mine))
+        if rank == 0:
+            gathered.sort(key=lambda g: g[0])
+            got = np.concatenate([g[2] for g in gathered])
+            q.put((rank, bool(np.array_equal(got, oracle.pfb(x, P, T, h))), [g[:2] for g in gathered]))
+        else:
+            q.put((rank, None, None))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_stream_two_ranks_gloo():
+    """World size 2: each rank channelises its share of one stream from its
+    halo'd slice; the shares gathered on rank 0 equal the whole output."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted([q.get(timeout=120) for _ in procs], key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert res[0][1] is True
+    assert res[0][2] == [(0, 99), (99, 197)]
