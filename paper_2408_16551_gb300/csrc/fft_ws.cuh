@@ -555,26 +555,27 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
 #pragma unroll
                     for (int b = 0; b < NB; ++b) h[m][b] = __ldg(d.taps + m * P + branch(b >> 1, b & 1));
             }
-            const int64_t nspec = sB - sA;
-            const int64_t nfr = nspec + TT - 1;
+            // segment-relative counters fit 32 bits: a segment is at most one
+            // CTA's range (units_per_cta, checked on the host)
+            const int nspec = (int)(sB - sA);
+            const int nfr = nspec + TT - 1;
             float2 *out_seg = d.out + sA * d.ldo;
-            int64_t first_row_spec = 0;  // segment-relative spectrum of the batch's first row
-            for (int64_t i0 = 0; i0 < nfr && ok; i0 += TT) {
+            int first_row_spec = 0;  // segment-relative spectrum of the batch's first row
+            for (int i0 = 0; i0 < nfr && ok; i0 += TT) {
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
-                    const int64_t i = i0 + k;
-                    if (i < nfr && ok) {
+                    const int i = i0 + k;
+                    if (i < nfr) {
                         // ---- frame i of the segment from the ring ----
                         const uint32_t slot = pc % NSLOT;
                         // warp-uniform decision: every lane takes the same path
                         if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * slot, (pc / NSLOT) & 1))) {
                             *abort_flag = 1;
                             ok = false;
+                            break;
                         }
                         float2 v[NB];
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) v[b] = make_float2(0.f, 0.f);
-                        if (ok) {
+                        {
                             const uint8_t *fr = ring + slot * C::FB;
                             const float sc = d.scale;
 #pragma unroll
@@ -635,8 +636,8 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                 pend[js][b] = fma2(make_float2(h[m][b], h[m][b]), v[b], pend[js][b]);
                         }
                         // ---- spectrum i - TT + 1 is complete ----
-                        const int64_t jspec = i - (TT - 1);
-                        if (ok && jspec >= 0) {
+                        const int jspec = i - (TT - 1);
+                        if (jspec >= 0) {
                             const int jslot = ((k + 1) % TT);
                             if (brow == 0) {
                                 // new batch: wait until the FFT warps have released this Y buffer
@@ -644,10 +645,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                     !__all_sync(0xffffffffu, mbar_wait(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
                                     *abort_flag = 1;
                                     ok = false;
+                                    break;
                                 }
                                 first_row_spec = jspec;
                             }
-                            if (!ok) break;
                             if constexpr (C::DIF4) {
                                 // radix-4 DIF butterfly on y[t + k Q], k = 0..3
                                 float2 *ysub = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF) +
@@ -670,7 +671,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                             ++brow;
                             if (brow == SB || jspec == nspec - 1) {
                                 if (t == 0) {
-                                    meta[bc & 1].out = out_seg + first_row_spec * d.ldo;
+                                    meta[bc & 1].out = out_seg + (int64_t)first_row_spec * d.ldo;
                                     meta[bc & 1].ldo = d.ldo;
                                     meta[bc & 1].nrows = brow;
                                 }
@@ -793,6 +794,8 @@ static pfb_status launch_fft_ws_k(LaunchArgs &a, cudaStream_t stream) {
     }
     int64_t grid = a.nunits < grid_cap ? a.nunits : grid_cap;
     if (grid < 1) return PFB_OK;
+    if ((a.nunits + grid - 1) / grid > INT32_MAX - 64)  // segment counters are 32-bit in the kernel
+        return fail(PFB_ERR_INVALID, "too many spectra for one launch of k_fft_ws");
     a.units_per_cta = (int32_t)((a.nunits + grid - 1) / grid);
     grid = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
     k<<<(unsigned)grid, C::NTHREADS, C::SMEM, stream>>>(a);
