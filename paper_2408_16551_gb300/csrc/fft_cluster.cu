@@ -45,6 +45,8 @@ static pfb_status launch_ws_cluster_k(LaunchArgs &a, cudaStream_t stream) {
     }
     int64_t clusters = a.nunits < cap_clusters ? a.nunits : cap_clusters;
     if (clusters < 1) return PFB_OK;
+    if ((a.nunits + clusters - 1) / clusters > INT32_MAX - 64)  // 32-bit segment counters in the kernels
+        return fail(PFB_ERR_INVALID, "too many spectra for one cluster launch");
     a.units_per_cta = (int32_t)((a.nunits + clusters - 1) / clusters);
     clusters = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
     cfg.gridDim = dim3((unsigned)(clusters * CS), 1, 1);
@@ -103,6 +105,8 @@ static pfb_status launch_cluster_k(LaunchArgs &a, cudaStream_t stream) {
     }
     int64_t clusters = a.nunits < cap_clusters ? a.nunits : cap_clusters;
     if (clusters < 1) return PFB_OK;
+    if ((a.nunits + clusters - 1) / clusters > INT32_MAX - 64)  // 32-bit segment counters in the kernels
+        return fail(PFB_ERR_INVALID, "too many spectra for one cluster launch");
     a.units_per_cta = (int32_t)((a.nunits + clusters - 1) / clusters);
     clusters = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
     cfg.gridDim = dim3((unsigned)(clusters * CS), 1, 1);

@@ -149,26 +149,30 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
             int64_t rA, rB;
             sy_rows(fA, fB, TT, d.n_frames, rA, rB);
             const int64_t s_first = fA - TT + 1;
-            const int64_t nfr = fB - s_first;            // rows s_first .. fB-1
-            int64_t batch_rows = min((int64_t)SB, rB - rA);  // rows of the current batch
-            int64_t done_rows = 0;                           // real rows consumed in this segment
+            // segment-relative counters fit 32 bits: a segment is at most one
+            // CTA's range of output frames (units_per_cta, checked on the host)
+            const int nfr = (int)(fB - s_first);             // rows s_first .. fB-1
+            const int iA = (int)(rA - s_first), iB = (int)(rB - s_first);  // rows that exist
+            int batch_rows = (int)min((int64_t)SB, rB - rA);   // rows of the current batch
+            int done_rows = 0;                                 // real rows consumed in this segment
+            float2 *o_seg = d.out + s_first * (int64_t)P + t;
 #pragma unroll 1
-            for (int64_t i0 = 0; i0 < nfr && ok; i0 += TT) {
+            for (int i0 = 0; i0 < nfr && ok; i0 += TT) {
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
-                    const int64_t i = i0 + k;
-                    if (i < nfr && ok) {
-                        const int64_t s = s_first + i;
+                    const int i = i0 + k;
+                    if (i < nfr) {
                         float2 yv[NB];
 #pragma unroll
                         for (int kk = 0; kk < NB; ++kk) yv[kk] = make_float2(0.f, 0.f);
-                        if (s >= rA && s < rB) {
+                        if (i >= iA && i < iB) {
                             if (urow == 0 &&
                                 !__all_sync(0xffffffffu, mbar_wait(ufull0 + 8 * (bc & 1), (bc >> 1) & 1))) {
                                 *abort_flag = 1;
                                 ok = false;
+                                break;
                             }
-                            if (ok) {
+                            {
                                 const float2 *ur = U + ((bc & 1) * SB + urow) * 4 * Q + t;
                                 const float2 u0 = ur[0], u1 = ur[Q], u2 = ur[2 * Q], u3 = ur[3 * Q];
                                 // y~[t + Q kk] = sum_k1 i^(kk k1) U_k1[t]
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
                                     if (lane == 0) mbar_arrive(uempty0 + 8 * (bc & 1));
                                     ++bc;
                                     urow = 0;
-                                    batch_rows = min((int64_t)SB, rB - rA - done_rows);
+                                    batch_rows = min(SB, iB - iA - done_rows);
                                 }
                             }
                         }
@@ -202,8 +206,8 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
                             for (int kk = 0; kk < NB; ++kk)
                                 pend[js][kk] = fma2(make_float2(hs[m][kk], hs[m][kk]), yv[kk], pend[js][kk]);
                         }
-                        if (ok && s >= fA) {
-                            float2 *o = d.out + s * (int64_t)P + t;
+                        if (i >= TT - 1) {  // frame s_first + i = fA + (i - TT + 1) is complete
+                            float2 *o = o_seg + (int64_t)i * P;
 #pragma unroll
                             for (int kk = 0; kk < NB; ++kk) store_cs(o + Q * kk, pend[k][kk]);
                         }

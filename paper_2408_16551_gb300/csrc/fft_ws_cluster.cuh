@@ -273,22 +273,23 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN, TC>::NTHREADS, 1)
 #pragma unroll
                     for (int j = 0; j < NB; ++j) h[m][j] = __ldg(d.taps + m * P + crank * PL + t + Q * j);
             }
-            const int64_t nspec = sB - sA;
-            const int64_t nfr = nspec + TT - 1;
-            for (int64_t i0 = 0; i0 < nfr && ok; i0 += TT) {
+            // segment-relative counters fit 32 bits: a segment is at most one
+            // cluster's range (units_per_cta, checked on the host)
+            const int nspec = (int)(sB - sA);
+            const int nfr = nspec + TT - 1;
+            for (int i0 = 0; i0 < nfr && ok; i0 += TT) {
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
-                    const int64_t i = i0 + k;
-                    if (i < nfr && ok) {
+                    const int i = i0 + k;
+                    if (i < nfr) {
                         const uint32_t slot = pc % NSLOT;
                         if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * slot, (pc / NSLOT) & 1))) {
                             *abort_flag = 1;
                             ok = false;
+                            break;
                         }
                         float2 v[NB];
-#pragma unroll
-                        for (int j = 0; j < NB; ++j) v[j] = make_float2(0.f, 0.f);
-                        if (ok) {
+                        {
                             const uint8_t *fr = ring + slot * C::FB;
                             const float sc = d.scale;
 #pragma unroll
@@ -319,8 +320,8 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN, TC>::NTHREADS, 1)
                             for (int j = 0; j < NB; ++j)
                                 pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
                         }
-                        const int64_t jspec = i - (TT - 1);
-                        if (ok && jspec >= 0) {
+                        const int jspec = i - (TT - 1);
+                        if (jspec >= 0) {
                             const int jslot = (k + 1) % TT;
                             // every CTA's cross step consumed this X buffer's previous batch
                             if (brow == 0 && bc >= 2 &&
@@ -328,8 +329,8 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN, TC>::NTHREADS, 1)
                                             mbar_wait(xempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
                                 *abort_flag = 1;
                                 ok = false;
+                                break;
                             }
-                            if (!ok) break;
                             push(brow, pend[jslot][0], pend[jslot][1], pend[jslot][2], pend[jslot][3]);
                             if (++brow == SB) {
                                 ++bc;

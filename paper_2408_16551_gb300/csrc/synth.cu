@@ -25,6 +25,8 @@ static pfb_status launch_synth_k(LaunchArgs &a, cudaStream_t stream) {
     }
     int64_t grid = a.nunits < grid_cap ? a.nunits : grid_cap;
     if (grid < 1) return PFB_OK;
+    if ((a.nunits + grid - 1) / grid > INT32_MAX - 64)  // 32-bit segment counters in the kernel
+        return fail(PFB_ERR_INVALID, "too many output frames for one launch of k_synth_ws");
     a.units_per_cta = (int32_t)((a.nunits + grid - 1) / grid);
     grid = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
     k<<<(unsigned)grid, C::NTHREADS, C::SMEM, stream>>>(a);
