@@ -65,6 +65,7 @@ struct WsCfg {
     // with setmaxnreg the producer sits in a warpgroup of its own (3 idle warps)
     static constexpr int NTHREADS = NFT + NFFTT + (SETMAXNREG ? 128 : 32);
     static constexpr int SB = 4;                                     // spectra per FFT batch
+    static_assert(TT % SB == 0, "batch rows follow the frame loop's unrolling");
     static constexpr int MR = 16;
     static constexpr int G = 16;
     static constexpr int YROW = P + P / G;
@@ -542,7 +543,6 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         int cur = -1;
         uint32_t pc = 0;   // frames consumed
         uint32_t bc = 0;   // batches produced
-        int brow = 0;      // rows written into the current batch
         bool ok = true;
         int si;
         int64_t sA, sB;
@@ -560,7 +560,6 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
             const int nspec = (int)(sB - sA);
             const int nfr = nspec + TT - 1;
             float2 *out_seg = d.out + sA * d.ldo;
-            int first_row_spec = 0;  // segment-relative spectrum of the batch's first row
             for (int i0 = 0; i0 < nfr && ok; i0 += TT) {
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
@@ -639,15 +638,15 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                         const int jspec = i - (TT - 1);
                         if (jspec >= 0) {
                             const int jslot = ((k + 1) % TT);
-                            if (brow == 0) {
-                                // new batch: wait until the FFT warps have released this Y buffer
-                                if (bc >= 2 &&
-                                    !__all_sync(0xffffffffu, mbar_wait(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
-                                    *abort_flag = 1;
-                                    ok = false;
-                                    break;
-                                }
-                                first_row_spec = jspec;
+                            // row of the batch: every segment's batches start at its spectrum 0
+                            // and SB divides TT, so the row is (k + 1) mod SB, fixed at compile time
+                            const int brow = (k + 1) % SB;
+                            // new batch: wait until the FFT warps have released this Y buffer
+                            if (brow == 0 && bc >= 2 &&
+                                !__all_sync(0xffffffffu, mbar_wait(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
+                                *abort_flag = 1;
+                                ok = false;
+                                break;
                             }
                             if constexpr (C::DIF4) {
                                 // radix-4 DIF butterfly on y[t + k Q], k = 0..3
@@ -668,17 +667,15 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
 #pragma unroll
                                 for (int b = 0; b < NB; ++b) yrow[ypad<G>(branch(b >> 1, b & 1))] = pend[jslot][b];
                             }
-                            ++brow;
-                            if (brow == SB || jspec == nspec - 1) {
+                            if (brow == SB - 1 || jspec == nspec - 1) {
                                 if (t == 0) {
-                                    meta[bc & 1].out = out_seg + (int64_t)first_row_spec * d.ldo;
+                                    meta[bc & 1].out = out_seg + (int64_t)(jspec - brow) * d.ldo;
                                     meta[bc & 1].ldo = d.ldo;
-                                    meta[bc & 1].nrows = brow;
+                                    meta[bc & 1].nrows = brow + 1;
                                 }
                                 __syncwarp();
                                 if (lane == 0) mbar_arrive(yfull0 + 8 * (bc & 1));
                                 ++bc;
-                                brow = 0;
                             }
                         }
                     }
