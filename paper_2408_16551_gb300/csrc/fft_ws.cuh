@@ -209,7 +209,6 @@ __device__ __forceinline__ void ws_dif4_last(const float2 *src, const float2 *tw
     constexpr int STRIDE = Q / R;
     static_assert(STRIDE == NS && STRIDE % G == 0, "last pass");
     constexpr int NBF = SB * 4 * STRIDE;
-    constexpr int P = 4 * Q;
     const float2 *twp = tw + fft_tw_offset(Q, PASS, MR);
 #pragma unroll 1
     for (int b = ft; b < NBF; b += nft) {
@@ -540,6 +539,13 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         };
         float h[TT][NB];
         float2 pend[TT][NB];
+        // DIF4: this thread's twiddles w_P^(t k1), k1 = 1..3, applied to the
+        // butterfly outputs before they are handed over
+        float2 wt[3];
+        if constexpr (C::DIF4) {
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) wt[k1 - 1] = tw[fft_tw_entries(C::Q, C::MR) + (k1 - 1) * C::Q + t];
+        }
         int cur = -1;
         uint32_t pc = 0;   // frames consumed
         uint32_t bc = 0;   // batches produced
@@ -658,10 +664,9 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                 const float2 a3 = csub2(pend[jslot][1], pend[jslot][3]);
                                 const float2 mi_a3 = make_float2(a3.y, -a3.x);  // -i a3
                                 ysub[0] = cadd2(a0, a2);
-                                // the twiddles w_P^(t k1) are applied by the FFT warps' first pass
-                                ysub[C::SROW] = cadd2(a1, mi_a3);
-                                ysub[2 * C::SROW] = csub2(a0, a2);
-                                ysub[3 * C::SROW] = csub2(a1, mi_a3);
+                                ysub[C::SROW] = cmul(cadd2(a1, mi_a3), wt[0]);
+                                ysub[2 * C::SROW] = cmul(csub2(a0, a2), wt[1]);
+                                ysub[3 * C::SROW] = cmul(csub2(a1, mi_a3), wt[2]);
                             } else {
                                 float2 *yrow = Y + (bc & 1) * (SB * YROW) + brow * YROW;
 #pragma unroll
@@ -711,8 +716,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                 float2 *Yb = Y + (bc & 1) * (SB * YROW);
                 if constexpr (C::DIF4) {
                     Yb = reinterpret_cast<float2 *>(ws_smem + C::OFF_Y + (bc & 1) * C::YBUF);
-                    ws_pass<C::Q, C::MR, 4 * SB, 0, false, C::SROW, G, true>(
-                        Yb, W, tw, nullptr, 0, ft, C::NFFTT, tw + fft_tw_entries(C::Q, C::MR));
+                    ws_pass<C::Q, C::MR, 4 * SB, 0, false, C::SROW, G>(Yb, W, tw, nullptr, 0, ft, C::NFFTT);
                     named_bar_sync<1>(C::NFFTT);
                     if (ft == 0) mbar_arrive(yempty0 + 8 * (bc & 1));  // Y has been read
                     ws_dif4_last<C::Q, SB, C::SROW, G>(W, tw, mt.out, mt.nrows, ft, C::NFFTT, mt.ldo);
