@@ -26,9 +26,9 @@
 // (setmaxnreg): 256*208 + 128*72 + 128*24 = 512*128 registers at launch.
 // P = 1024 splits the DFT once more (decimation in frequency by 4): FIR thread
 // t owns branches t + k*P/4 (k = 0..3) and hands over the radix-4 butterfly
-// of its four branch sums; the FFT warps multiply by w_P^(t k1) in their
-// first pass and finish four P/4-point transforms (Y -> W -> HBM), bin
-// 4m + k1 coming from sub-transform k1.  Otherwise thread t owns the branch
+// of its four branch sums, output k1 already multiplied by w_P^(t k1); the
+// FFT warps finish four P/4-point transforms (Y -> W -> HBM), bin 4m + k1
+// coming from sub-transform k1.  Otherwise thread t owns the branch
 // pairs (2t, 2t+1) + k*P/NPAIR.  Either way its ring reads and branch-sum
 // writes are contiguous across the warp (no shared-memory bank conflicts).
 #pragma once
