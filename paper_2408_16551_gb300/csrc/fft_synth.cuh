@@ -10,7 +10,7 @@
 // P = 4Q (Q = 128 or 256).  The inverse DFT is decimated in time once,
 // k = 4m + k1:
 //   V_k1[t]        = sum_{m<Q} X[4m + k1] exp(+2 pi i t m / Q)       IFFT warps
-//   U_k1[t]        = exp(+2 pi i t k1 / P) V_k1[t]                   IFFT warps
+//   U_k1[t]        = exp(+2 pi i t k1 / P) V_k1[t]                   FIR warps
 //   y~[t + Q kk]   = (1/P) sum_{k1<4} i^(kk k1) U_k1[t]              FIR warps
 // and the 1/P is folded into the taps (exact: P is a power of two).  The IFFT
 // warps run the forward Stockham passes on conjugated values (V = conj(FFT(
@@ -19,9 +19,9 @@
 //       a ring of NSLOT slots;
 //   IFFT warps (128 threads): batches of SB rows; pass 0 (radix 16) reads the
 //       four interleaved sub-rows straight from the ring, pass 1 finishes the
-//       Q-point transforms, applies the twiddles and writes U into a double-
-//       buffered batch buffer;
-//   FIR warps (Q threads, branches t + Q kk): the radix-4 step, then the
+//       Q-point transforms and writes V into a double-buffered batch buffer;
+//   FIR warps (Q threads, branches t + Q kk): the twiddles (three complex
+//       products per row; each thread's t is fixed), the radix-4 step, then the
 //       synthesis FIR with the T-1 pending output frames in registers (slot
 //       rotation at compile time, as in the analysis kernel); every row
 //       completes one output frame, stored with coalesced streaming stores.
@@ -130,6 +130,9 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
         const int t = threadIdx.x;
         float hs[TT][NB];
         float2 pend[TT][NB];
+        // this thread's twiddles w_P^(t k1), k1 = 1..3, in shared memory (read per
+        // row: holding them in registers spills the FIR state); U_k1 = conj(w) V_k1
+        const float2 *wt = tw + C::NTQ + t;
         int cur = -1;
         uint32_t bc = 0;   // batches consumed
         int urow = 0;      // rows consumed from the current batch
@@ -174,7 +177,8 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
                             }
                             {
                                 const float2 *ur = U + ((bc & 1) * SB + urow) * 4 * Q + t;
-                                const float2 u0 = ur[0], u1 = ur[Q], u2 = ur[2 * Q], u3 = ur[3 * Q];
+                                const float2 u0 = ur[0], u1 = cmul(ur[Q], conjf2(wt[0])),
+                                             u2 = cmul(ur[2 * Q], conjf2(wt[Q])), u3 = cmul(ur[3 * Q], conjf2(wt[2 * Q]));
                                 // y~[t + Q kk] = sum_k1 i^(kk k1) U_k1[t]
                                 const float2 a0 = cadd2(u0, u2), a1 = csub2(u0, u2);
                                 const float2 a2 = cadd2(u1, u3), a3 = csub2(u1, u3);
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
                     ok = false;
                     break;
                 }
-                // ---- pass 1: finish the Q-point transforms, twiddle w_P^(t k1), conjugate ----
+                // ---- pass 1: finish the Q-point transforms, conjugate ----
                 constexpr int NBF1 = SB * 4 * C::STRIDE1;
                 const float2 *twp = tw + fft_tw_offset(Q, 1, C::MR);
                 float2 *ub = U + (bc & 1) * SB * 4 * Q;
@@ -282,11 +286,7 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
                     dft_reg<C::R1, true>(v);
                     float2 *u = ub + (row * 4 + k1) * Q + j;
 #pragma unroll
-                    for (int r = 0; r < C::R1; ++r) {
-                        const int tt = j + 16 * r;
-                        const float2 z = k1 ? cmul(v[r], tw[C::NTQ + (k1 - 1) * Q + tt]) : v[r];
-                        u[16 * r] = conjf2(z);
-                    }
+                    for (int r = 0; r < C::R1; ++r) u[16 * r] = conjf2(v[r]);  // V_k1; the FIR warps twiddle it
                 }
                 named_bar_sync<1>(C::NIFT);  // U written, W free for the next pass 0
                 if (ft == 0) mbar_arrive(ufull0 + 8 * (bc & 1));
