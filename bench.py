@@ -207,11 +207,12 @@ def run_reference(args, rank, world):
     h = oracle.prototype(spec.P, spec.T, spec.window)
     xs = oracle.dequant(x, spec.in_dtype)
     ns = 64  # spectra per step: a bounded sample of the workload
+    n_windows = oracle.num_spectra(x.size, spec.P, spec.T) - ns + 1  # sample starts, wrapped for long runs
     for i in range(args.warmup):
-        oracle.pfb(xs, spec.P, spec.T, h, s0=i * ns, ns=ns)
+        oracle.pfb(xs, spec.P, spec.T, h, s0=(i * ns) % n_windows, ns=ns)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        oracle.pfb(xs, spec.P, spec.T, h, s0=(args.warmup + i) * ns, ns=ns)
+        oracle.pfb(xs, spec.P, spec.T, h, s0=((args.warmup + i) * ns) % n_windows, ns=ns)
     dt = (time.perf_counter() - t0) / args.steps
     value = ns * spec.P / dt / 1e9
     line = {
