@@ -637,7 +637,16 @@ def main():
                     err = sampled_rel_l2(outs[(max(3, args.steps // 4) - 1) % nsets], x, spec.in_dtype, P, T,
                                          spec.window, rows)
                     paths[name] = {"gsps": n / (ms * 1e-3) / 1e9, "rel_l2": err, "dtype": dt, "kernel": p2.kernel_name,
-                                   "ms_per_step": ms}
+                                   "variant": p2.variant, "ms_per_step": ms,
+                                   "hbm_frac": alg_bytes / (ms * 1e-3) / 1e9 / hbm}
+                    if path == pkg.PFB_DFT_GEMM_BF16X3 and p2.variant == 1:
+                        # factored tensor-core DFT: 1536 executed bf16 flop per sample (see the roofline note)
+                        tfl = n * 1536 / (ms * 1e-3) / 1e12
+                        paths[name]["tensor"] = {"executed_tflops": tfl, "frac_of_sustained_bf16": tfl / bf16s}
+                    elif path == pkg.PFB_DFT_GEMM_F32:
+                        # complex x complex FMA against the DFT matrix: 8P flop per sample on the FP32 SIMT cores
+                        tfl = n * 8 * P / (ms * 1e-3) / 1e12
+                        paths[name]["fp32_tflops"] = tfl
                     p2.close()
                 except pkg.PFBError as e:
                     paths[name] = {"gsps": None, "unavailable": str(e)}
