@@ -175,3 +175,68 @@ def test_sharded_stream_two_ranks_gloo():
         assert p.exitcode == 0
     assert res[0][1] is True
     assert res[0][2] == [(0, 99), (99, 197)]
+
+
+class _StubPlan:
+    """Stands in for a Plan in host-logic tests: records execute() calls."""
+
+    def __init__(self, P, T, in_dtype, hop=None):
+        self.P, self.T, self.in_dtype, self.hop = P, T, in_dtype, hop or P
+        self.calls = []
+
+    def out_spectra(self, n):
+        L = self.P * self.T
+        return 0 if n < L else (n - L) // self.hop + 1
+
+    def execute(self, x, out=None, stream=None):
+        self.calls.append((x, out))
+
+
+@pytest.mark.parametrize("P,T,in_dtype,hop,world", [(1024, 16, 1, None, 3), (1024, 16, 1, 512, 4),
+                                                    (4, 3, 2, None, 3), (16, 4, 0, None, 5)])
+def test_execute_sharded_stream_host_logic(P, T, in_dtype, hop, world):
+    """Each rank hands the plan the input slice of its spectra's windows (int8
+    input counts two values per sample) and the matching output rows; slice
+    starts keep 16-byte alignment."""
+    import torch
+    import paper_2408_16551_gb300 as pkg
+    esize = {pkg.PFB_IN_R32: 4, pkg.PFB_IN_C64: 8, pkg.PFB_IN_CI8: 2}[in_dtype]
+    k = 2 if in_dtype == pkg.PFB_IN_CI8 else 1
+    n = P * (T + 41) + 3
+    x = torch.arange(k * n)                                # element index = value
+    plan = _StubPlan(P, T, in_dtype, hop)
+    S = plan.out_spectra(n)
+    out = torch.zeros((S, P))
+    rows = []
+    for r in range(world):
+        s0, s1 = replicas.execute_sharded_stream(plan, x, out, r, world)
+        rows.append((s0, s1))
+    assert rows[0][0] == 0 and rows[-1][1] == S
+    assert all(rows[i][1] == rows[i + 1][0] for i in range(world - 1))
+    calls = [c for c in plan.calls]
+    assert len(calls) == sum(1 for s0, s1 in rows if s1 > s0)
+    for (xs, os_), (s0, s1) in zip(calls, [r for r in rows if r[1] > r[0]]):
+        a, b = int(xs[0]) // k, (int(xs[-1]) + 1) // k       # sample range of the slice
+        assert a == s0 * plan.hop and b == (s1 - 1) * plan.hop + P * T
+        assert (a * esize) % 16 == 0
+        assert plan.out_spectra(b - a) == s1 - s0
+        assert os_.shape[0] == s1 - s0 and os_.data_ptr() == out[s0].data_ptr()
+
+
+def test_execute_sharded_batch_host_logic(monkeypatch):
+    """Each rank passes exactly its dealt entries to one batch call."""
+    import torch
+    import paper_2408_16551_gb300 as pkg
+    calls = []
+    monkeypatch.setattr(pkg, "pfb_execute_batch", lambda entries, stream=None: calls.append(list(entries)))
+    sizes = [5000, 70, 1 << 16, 3000, 12, 40000, 999]
+    entries = [(_StubPlan(16, 4, pkg.PFB_IN_C64), torch.empty(m, dtype=torch.complex64), None) for m in sizes]
+    world = 3
+    ran = []
+    for r in range(world):
+        mine = replicas.execute_sharded_batch(entries, r, world)
+        assert mine == replicas.shard_streams(sizes, r, world)
+        ran += mine
+        assert [id(e) for e in calls[-1]] == [id(entries[i]) for i in mine]
+    assert sorted(ran) == list(range(len(sizes)))
+    assert len(calls) == world
