@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define PFB_API_VERSION 2
+#define PFB_API_VERSION 3
 
 #if defined(__GNUC__)
 #define PFB_API __attribute__((visibility("default")))
@@ -129,6 +129,32 @@ PFB_API pfb_status pfb_plan_create(const pfb_plan_desc *desc, pfb_plan_t *out_pl
  * still uses the plan.  NULL is accepted. */
 PFB_API pfb_status pfb_plan_destroy(pfb_plan_t plan);
 
+/* Kernel-side status of the plan's launches.  Every kernel bounds its
+ * device-side waits (1 s of %globaltimer by default); a wait that runs out
+ * makes the kernel wind down and write an error code into the plan's error
+ * word, which lives in mapped, pinned host memory.  This call reads and
+ * clears that word without blocking or synchronising: PFB_OK if no launch of
+ * the plan has failed since the last read, PFB_ERR_TIMEOUT if a device-side
+ * wait ran out, PFB_ERR_INTERNAL for any other kernel error code.  Call it
+ * after the work of interest has completed (e.g. after a stream or event
+ * synchronisation); the word is shared by all launches of the plan, so a
+ * failure cannot be attributed to one of several overlapping launches.
+ * pfb_execute_host and pfb_execute_host_noalloc read and clear the word
+ * themselves before returning; the server gives every batch its own word. */
+PFB_API pfb_status pfb_plan_status(pfb_plan_t plan);
+
+/* Test hook for the error reporting above (no paper counterpart; the
+ * failure-detection path of the channeliser).  mode 1 makes the producer
+ * role of the single-CTA warp-specialised FFT kernel (FFT path, P = 1024,
+ * variant 5) issue no input copies, so every consumer's bounded wait runs
+ * out after wait_ns nanoseconds and the launch reports PFB_ERR_TIMEOUT; no
+ * memory is touched and no GPU fault is provoked.  mode 0 restores normal
+ * operation.  wait_ns (0 = the default of 1 s, at most 10 s) bounds the
+ * device-side waits of the plan's launches in either mode; kernels other
+ * than that one ignore the mode and keep the default bound.
+ * Errors: PFB_ERR_INVALID for an unknown mode or wait_ns out of range. */
+PFB_API pfb_status pfb_plan_set_fault(pfb_plan_t plan, int32_t mode, int64_t wait_ns);
+
 /* Spectra produced for n_samples input samples: max(0, floor(n/P) - T + 1)
  * (Sec. 5.2 valid outputs, hop P); with a hop D < P, floor((n - P*T)/D) + 1
  * for n >= P*T, else 0.  Returns -1 for a NULL plan or n < 0. */
@@ -142,7 +168,9 @@ PFB_API pfb_status pfb_plan_get_taps(pfb_plan_t plan, double *host_out, int64_t 
  * d_in: n_samples samples in the plan's in_dtype (device memory).
  * d_out: complex64 [out_cap_spectra][P] (device memory); S rows are written.
  * Errors: PFB_ERR_INVALID if out_cap_spectra < S, pointers misaligned or NULL
- * while S > 0; PFB_ERR_CUDA if the launch fails.  S == 0 is valid (no-op). */
+ * while S > 0; PFB_ERR_CUDA if the launch fails.  S == 0 is valid (no-op).
+ * A failure inside the kernel (a bounded device-side wait that ran out) is
+ * reported afterwards, once the work has completed, by pfb_plan_status. */
 PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samples,
                        void *d_out, int64_t out_cap_spectra, void *cuda_stream);
 
@@ -152,7 +180,9 @@ PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samp
  * copies on an internal stream, kernels on cuda_stream, device->host copies
  * on a second internal stream, so both copy directions and the kernels
  * overlap; it starts after the work already queued on cuda_stream.  Results
- * equal those of pfb_execute.  Pinned host memory gives the fastest copies. */
+ * equal those of pfb_execute.  Pinned host memory gives the fastest copies.
+ * Returns PFB_ERR_TIMEOUT (output not valid) if a device-side wait of a
+ * kernel ran out; the plan's error word is cleared by the call. */
 PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples,
                             void *host_out, int64_t out_cap_spectra, void *cuda_stream);
 
@@ -175,15 +205,18 @@ PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_
  * order on cuda_stream (after the work already queued there); the call
  * returns once host_out is written.  No cudaMalloc, cudaFree, stream or event
  * creation happens in the call.
- *  - The first call on a device looks up the area's device address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make
- *    that first call before any stream capture begins.
+ *  - The area's device address is looked up (cudaGetSymbolAddress, with
+ *    the device current) and cached by pfb_plan_create on the plan's device.
+ *    That lookup loads the module holding the area: under CUDA's lazy module
+ *    loading this is when the device reserves the 32 MiB, so it happens at
+ *    the first plan creation on a device, never inside this entry point.
  *  - Every call on a device shares the one area, which keeps the last call's
  *    contents.  Calls whose work overlaps on the GPU (several host threads,
  *    or several streams) race on it: serialise them.
- * Errors: as pfb_execute_host; PFB_ERR_INVALID also when the staged input
- * (rounded up to 256 bytes) plus the output exceed PFB_NOALLOC_SCRATCH_BYTES,
- * with nothing launched. */
+ * Errors: as pfb_execute_host (PFB_ERR_TIMEOUT from the kernel's error
+ * word included); PFB_ERR_INVALID also when the staged input (rounded up to
+ * 256 bytes) plus the output exceed PFB_NOALLOC_SCRATCH_BYTES, with nothing
+ * launched. */
 PFB_API pfb_status pfb_execute_host_noalloc(pfb_plan_t plan, const void *host_in, int64_t n_samples,
                                             void *host_out, int64_t out_cap_spectra, void *cuda_stream);
 
@@ -216,6 +249,21 @@ typedef struct pfb_batch_item {
  * Streams producing 0 spectra are skipped.  All plans must be on one device.
  * Results equal per-stream pfb_execute bit for bit. */
 PFB_API pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_items, void *cuda_stream);
+
+/* pfb_execute_batch from and to HOST memory: items[i].d_in and d_out are
+ * host pointers here (pinned memory copies fastest).  The streams are staged
+ * through device buffers the library owns (per device, grown with cudaMalloc
+ * and kept), in chunks of consecutive items of about 32 MB of input: chunk
+ * c's copy-in, kernels and copy-out run on a copy-in stream, cuda_stream and
+ * a copy-out stream, three chunks in flight, so copies in both directions
+ * overlap the kernels.  Starts after the work already queued on cuda_stream
+ * and returns once every output is in host memory.  Results equal those of
+ * pfb_execute_batch (and of pfb_execute per stream) bit for bit.  Calls on one
+ * device are serialised.  Oversampled plans return PFB_ERR_UNSUPPORTED.
+ * Errors: as pfb_execute_batch; PFB_ERR_OOM for the staging buffers;
+ * PFB_ERR_TIMEOUT if a device-side wait of a kernel ran out (every plan's
+ * error word is read and cleared). */
+PFB_API pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_t n_items, void *cuda_stream);
 
 /* A reusable batch: the launches of pfb_execute_batch captured once into a
  * CUDA graph (tile shapes from the autotuner cache), replayed by

@@ -40,7 +40,8 @@ EXPORTED = [
     "pfb_status_string", "pfb_last_error", "pfb_launch_count", "pfb_plan_kernel_name",
     "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
     "pfb_execute_host_noalloc", "pfb_stream_state_size", "pfb_stream_state_export", "pfb_stream_state_import",
-    "pfb_synth_out_samples", "pfb_synthesize",
+    "pfb_synth_out_samples", "pfb_synthesize", "pfb_plan_status", "pfb_plan_set_fault",
+    "pfb_execute_batch_host",
 ]
 
 
@@ -98,6 +99,8 @@ def lib() -> ctypes.CDLL:
         sig = {
             "pfb_plan_create": (st, [ctypes.POINTER(pfb_plan_desc), ctypes.POINTER(vp)]),
             "pfb_plan_destroy": (st, [vp]),
+            "pfb_plan_status": (st, [vp]),
+            "pfb_plan_set_fault": (st, [vp, i32, i64]),
             "pfb_out_spectra": (i64, [vp, i64]),
             "pfb_plan_get_taps": (st, [vp, ctypes.POINTER(ctypes.c_double), i64]),
             "pfb_execute": (st, [vp, vp, i64, vp, i64, vp]),
@@ -109,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "pfb_stream_state_export": (st, [vp, i64, vp, i64]),
             "pfb_stream_state_import": (st, [vp, i64, vp, i64]),
             "pfb_execute_batch": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
+            "pfb_execute_batch_host": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
             "pfb_batch_create": (st, [ctypes.POINTER(pfb_batch_item), i32, ctypes.POINTER(vp)]),
             "pfb_batch_launch": (st, [vp, vp]),
             "pfb_batch_destroy": (st, [vp]),
@@ -231,6 +235,17 @@ class Plan:
     def out_spectra(self, n_samples: int) -> int:
         return int(lib().pfb_out_spectra(self.handle, n_samples))
 
+    def status(self) -> int:
+        """pfb_plan_status: read and clear the kernel error word of the plan's
+        launches (PFB_OK, PFB_ERR_TIMEOUT, PFB_ERR_INTERNAL); non-blocking."""
+        return int(lib().pfb_plan_status(self.handle))
+
+    def set_fault(self, mode: int, wait_ns: int = 0):
+        """pfb_plan_set_fault: error-reporting test hook (mode 1: the producer of
+        the single-CTA warp-specialised FFT kernel issues no copies, so its
+        consumers' bounded waits of wait_ns run out; mode 0: normal)."""
+        _check(lib().pfb_plan_set_fault(self.handle, mode, wait_ns), "pfb_plan_set_fault")
+
     def taps(self) -> np.ndarray:
         """FP64 prototype filter h[0..P*T) as generated on the GPU."""
         h = np.zeros(self.P * self.T, dtype=np.float64)
@@ -313,6 +328,21 @@ def pfb_execute_batch(entries, stream=None):
     """entries: list of (Plan, input tensor, output tensor [>=S, P])."""
     arr = _items(entries)
     _check(lib().pfb_execute_batch(arr, len(entries), _stream_handle(stream)), "pfb_execute_batch")
+
+
+def pfb_execute_batch_host(entries, stream=None):
+    """entries: list of (Plan, host input ndarray, host output ndarray [>=S, P]
+    complex64); pfb_execute_batch_host stages them through the device and
+    returns once every output is written."""
+    arr = (pfb_batch_item * max(1, len(entries)))()
+    for i, (plan, x, out) in enumerate(entries):
+        n = x.size // 2 if plan.in_dtype == PFB_IN_CI8 else x.size
+        arr[i].plan = plan.handle.value
+        arr[i].d_in = x.ctypes.data
+        arr[i].n_samples = n
+        arr[i].d_out = out.ctypes.data if out is not None and out.size else None
+        arr[i].out_cap_spectra = (out.size // plan.P) if out is not None else 0
+    _check(lib().pfb_execute_batch_host(arr, len(entries), _stream_handle(stream)), "pfb_execute_batch_host")
 
 
 class Batch:

@@ -1,6 +1,8 @@
 // Host side of the C ABI: status strings, error messages, pfb_execute,
 // pfb_execute_host and the batched entry points (work grouping, CUDA graphs).
 #include <algorithm>
+#include <mutex>
+#include <vector>
 #include <cstring>
 #include <map>
 #include <new>
@@ -43,9 +45,42 @@ int64_t family_units(const Plan &plan, int64_t S) {
 
 const float *family_taps(const Plan &plan) { return plan.d_taps_pad ? plan.d_taps_pad : plan.d_taps; }
 
+pfb_status alloc_error_words(int n, int **h_err, int **d_err) {
+    *h_err = nullptr;
+    *d_err = nullptr;
+    void *h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, sizeof(int) * (size_t)n, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc (error words)");
+    std::memset(h, 0, sizeof(int) * (size_t)n);
+    void *d = nullptr;
+    e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        return cuda_fail(e, "cudaHostGetDevicePointer (error words)");
+    }
+    *h_err = static_cast<int *>(h);
+    *d_err = static_cast<int *>(d);
+    return PFB_OK;
+}
+
+void free_error_words(int *h_err) {
+    if (h_err) cudaFreeHost(h_err);
+}
+
+pfb_status take_kernel_error(int *h_err, const char *what) {
+    if (!h_err) return PFB_OK;
+    volatile int *w = h_err;
+    const int v = *w;
+    if (v == KERR_NONE) return PFB_OK;
+    *w = KERR_NONE;
+    if (v == KERR_TIMEOUT)
+        return fail(PFB_ERR_TIMEOUT, std::string(what) + ": a device-side wait of the kernel ran out (error word)");
+    return fail(PFB_ERR_INTERNAL, std::string(what) + ": the kernel reported error code " + std::to_string(v));
+}
+
 // Launch the plan's family kernel over n stream descriptors (all of this
 // family/P/T/dtype), in groups of kMaxStreamsPerLaunch.
-pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream) {
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err) {
     for (int g0 = 0; g0 < n; g0 += kMaxStreamsPerLaunch) {
         const int g1 = std::min(n, g0 + kMaxStreamsPerLaunch);
         LaunchArgs a;
@@ -64,7 +99,9 @@ pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_
         a.nunits = units;
         a.tw = plan.d_tw;
         a.aux = plan.d_dft;
-        a.err = plan.d_err;
+        a.err = err ? err : plan.d_err;
+        a.wait_ns = plan.wait_ns;
+        a.fault = plan.fault;
         pfb_status st;
         switch (plan.family) {
         case FAM_FFT_FAST: st = launch_fft_fast(plan, a, stream); break;
@@ -84,6 +121,7 @@ pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_
 pfb_status prepare_family(const Plan &plan) {
     LaunchArgs a;
     std::memset(&a, 0, sizeof(a));
+    a.wait_ns = kDefaultWaitNs;
     switch (plan.family) {
     case FAM_FFT_FAST: return launch_fft_fast(plan, a, nullptr);
     case FAM_FFT_GENERIC: return launch_fft_generic(plan, a, nullptr);
@@ -193,6 +231,23 @@ extern "C" const char *pfb_status_string(pfb_status s) {
 }
 
 extern "C" const char *pfb_last_error(void) { return t_err.c_str(); }
+
+extern "C" pfb_status pfb_plan_status(pfb_plan_t plan) {
+    clear_error();
+    if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
+    return take_kernel_error(reinterpret_cast<Plan *>(plan)->h_err, "pfb_plan_status");
+}
+
+extern "C" pfb_status pfb_plan_set_fault(pfb_plan_t plan, int32_t mode, int64_t wait_ns) {
+    clear_error();
+    if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
+    if (mode != FAULT_NONE && mode != FAULT_NO_COPIES) return fail(PFB_ERR_INVALID, "unknown fault mode");
+    if (wait_ns < 0 || wait_ns > 10ll * (int64_t)kDefaultWaitNs) return fail(PFB_ERR_INVALID, "wait_ns outside [0, 10 s]");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    p.fault = mode;
+    p.wait_ns = wait_ns == 0 ? kDefaultWaitNs : (uint64_t)wait_ns;
+    return PFB_OK;
+}
 extern "C" int64_t pfb_launch_count(void) { return g_launches.load(); }
 
 extern "C" pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samples, void *d_out,
@@ -292,7 +347,7 @@ extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int
     PFB_CUDA_TRY(cudaEventRecord(ev_done, p.s_copy_out));
     PFB_CUDA_TRY(cudaStreamWaitEvent(s, ev_done, 0));
     PFB_CUDA_TRY(cudaStreamSynchronize(s));
-    return PFB_OK;
+    return take_kernel_error(p.h_err, "pfb_execute_host");
 }
 
 // ---------------------------------------------------------------------------
@@ -354,6 +409,198 @@ extern "C" pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_i
         if (st != PFB_OK) return st;
     }
     return PFB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pfb_execute_batch_host: a batch from and to host memory, pipelined
+// ---------------------------------------------------------------------------
+namespace pfb {
+
+// Per-device staging for host batches: kHostSlots chunk slots (input and
+// output areas), a copy-in and a copy-out stream, per-slot events.
+struct HostBatchCtx {
+    static constexpr int kHostSlots = 3;
+    std::mutex mu;
+    bool ready = false;
+    void *d_in[kHostSlots] = {}, *d_out[kHostSlots] = {};
+    size_t in_cap[kHostSlots] = {}, out_cap[kHostSlots] = {};
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[kHostSlots] = {}, ev_k[kHostSlots] = {}, ev_free[kHostSlots] = {};
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
+constexpr int kHostCtxDevices = 64;
+static HostBatchCtx g_host_ctx[kHostCtxDevices];
+
+static size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+
+static pfb_status grow(void **p, size_t *cap, size_t need) {
+    if (*cap >= need) return PFB_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PFB_ERR_OOM, "host-batch staging buffer");
+    }
+    *cap = need;
+    return PFB_OK;
+}
+
+}  // namespace pfb
+
+extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_t n_items, void *cuda_stream) {
+    clear_error();
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(PFB_ERR_INVALID, "bad item list");
+    // validate every item before anything is copied or launched
+    int device = -1;
+    std::vector<int64_t> S(n_items), fr_bytes(n_items);
+    for (int i = 0; i < n_items; ++i) {
+        const pfb_batch_item &it = items[i];
+        if (!it.plan) return fail(PFB_ERR_INVALID, "item with NULL plan");
+        const Plan &p = *reinterpret_cast<Plan *>(it.plan);
+        if (device < 0) device = p.device;
+        if (p.device != device) return fail(PFB_ERR_INVALID, "batch items span devices");
+        if (p.R > 1) return fail(PFB_ERR_UNSUPPORTED, "oversampled plans (hop < P) run through pfb_execute_batch");
+        if (it.n_samples < 0) return fail(PFB_ERR_INVALID, "item " + std::to_string(i) + ": n_samples < 0");
+        S[i] = out_spectra(p, it.n_samples);
+        fr_bytes[i] = (it.n_samples / p.P) * p.P * (int64_t)p.esize;  // whole frames only
+        if (S[i] == 0) continue;
+        if (!it.d_in || !it.d_out) return fail(PFB_ERR_INVALID, "item " + std::to_string(i) + ": NULL buffer with S > 0");
+        if (it.out_cap_spectra < S[i])
+            return fail(PFB_ERR_INVALID, "item " + std::to_string(i) + ": out_cap_spectra smaller than the spectra produced");
+    }
+    if (device < 0) return PFB_OK;
+    if (device >= kHostCtxDevices) return fail(PFB_ERR_INVALID, "device ordinal out of range");
+    // chunks: runs of consecutive items of about kChunkBytes of input
+    constexpr int64_t kChunkBytes = 32ll << 20;
+    struct Chunk { int i0, i1; size_t in_bytes, out_bytes; };
+    std::vector<Chunk> chunks;
+    for (int i = 0; i < n_items;) {
+        if (S[i] == 0) { ++i; continue; }
+        Chunk c{i, i, 0, 0};
+        while (c.i1 < n_items) {
+            const int j = c.i1;
+            if (S[j] > 0) {
+                const Plan &p = *reinterpret_cast<Plan *>(items[j].plan);
+                const size_t ib = round256((size_t)fr_bytes[j]);
+                if (c.i1 > c.i0 && (int64_t)(c.in_bytes + ib) > kChunkBytes) break;
+                c.in_bytes += ib;
+                c.out_bytes += round256((size_t)S[j] * p.P * sizeof(float2));
+            }
+            ++c.i1;
+        }
+        chunks.push_back(c);
+        i = c.i1;
+    }
+    if (chunks.empty()) return PFB_OK;
+    HostBatchCtx &x = g_host_ctx[device];
+    std::lock_guard<std::mutex> lk(x.mu);
+    DeviceGuard g(device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!x.ready) {
+        PFB_CUDA_TRY(cudaStreamCreateWithFlags(&x.s_in, cudaStreamNonBlocking));
+        PFB_CUDA_TRY(cudaStreamCreateWithFlags(&x.s_out, cudaStreamNonBlocking));
+        for (int b = 0; b < HostBatchCtx::kHostSlots; ++b) {
+            PFB_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_in[b], cudaEventDisableTiming));
+            PFB_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_k[b], cudaEventDisableTiming));
+            PFB_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_free[b], cudaEventDisableTiming));
+        }
+        PFB_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_start, cudaEventDisableTiming));
+        PFB_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_done, cudaEventDisableTiming));
+        x.ready = true;
+    }
+    size_t need_in = 0, need_out = 0;
+    for (const Chunk &c : chunks) {
+        need_in = std::max(need_in, c.in_bytes);
+        need_out = std::max(need_out, c.out_bytes);
+    }
+    // slots in use by an earlier call have finished (the call returns after
+    // its last copy), so growing them here is safe
+    for (int b = 0; b < HostBatchCtx::kHostSlots && b < (int)chunks.size(); ++b) {
+        pfb_status st = grow(&x.d_in[b], &x.in_cap[b], need_in);
+        if (st == PFB_OK) st = grow(&x.d_out[b], &x.out_cap[b], need_out);
+        if (st != PFB_OK) return st;
+    }
+    // Chunk c uses slot c mod kHostSlots: its copy-in waits until the slot's
+    // previous chunk has been copied out; its kernels run on the caller's
+    // stream after its copy-in; its copy-out follows its kernels.
+    PFB_CUDA_TRY(cudaEventRecord(x.ev_start, s));
+    PFB_CUDA_TRY(cudaStreamWaitEvent(x.s_in, x.ev_start, 0));
+    PFB_CUDA_TRY(cudaStreamWaitEvent(x.s_out, x.ev_start, 0));
+    std::vector<pfb_batch_item> dev_items;
+    pfb_status st = PFB_OK;
+    for (size_t c = 0; c < chunks.size() && st == PFB_OK; ++c) {
+        const Chunk &ch = chunks[c];
+        const int b = (int)(c % HostBatchCtx::kHostSlots);
+        if (c >= (size_t)HostBatchCtx::kHostSlots) {
+            cudaError_t e = cudaStreamWaitEvent(x.s_in, x.ev_free[b], 0);
+            if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamWaitEvent"); break; }
+        }
+        char *din = static_cast<char *>(x.d_in[b]);
+        char *dout = static_cast<char *>(x.d_out[b]);
+        dev_items.clear();
+        size_t oi = 0, oo = 0;
+        for (int i = ch.i0; i < ch.i1 && st == PFB_OK; ++i) {
+            if (S[i] == 0) continue;
+            const Plan &p = *reinterpret_cast<Plan *>(items[i].plan);
+            cudaError_t e = cudaMemcpyAsync(din + oi, items[i].d_in, (size_t)fr_bytes[i], cudaMemcpyHostToDevice, x.s_in);
+            if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemcpyAsync (host batch input)"); break; }
+            pfb_batch_item d = items[i];
+            d.d_in = din + oi;
+            d.n_samples = fr_bytes[i] / p.esize;
+            d.d_out = dout + oo;
+            d.out_cap_spectra = S[i];
+            dev_items.push_back(d);
+            oi += round256((size_t)fr_bytes[i]);
+            oo += round256((size_t)S[i] * p.P * sizeof(float2));
+        }
+        if (st != PFB_OK) break;
+        cudaError_t e = cudaEventRecord(x.ev_in[b], x.s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, x.ev_in[b], 0);
+        if (e != cudaSuccess) { st = cuda_fail(e, "host batch copy-in event"); break; }
+        std::vector<Group> groups;
+        int dev2 = -1;
+        st = build_groups(dev_items.data(), (int32_t)dev_items.size(), groups, dev2);
+        for (auto &gr : groups) {
+            if (st != PFB_OK) break;
+            st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), s);
+        }
+        if (st != PFB_OK) break;
+        e = cudaEventRecord(x.ev_k[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(x.s_out, x.ev_k[b], 0);
+        if (e != cudaSuccess) { st = cuda_fail(e, "host batch kernel event"); break; }
+        for (size_t k = 0, i = ch.i0; i < (size_t)ch.i1 && st == PFB_OK; ++i) {
+            if (S[i] == 0) continue;
+            const Plan &p = *reinterpret_cast<Plan *>(items[i].plan);
+            e = cudaMemcpyAsync(items[i].d_out, dev_items[k].d_out, (size_t)S[i] * p.P * sizeof(float2),
+                                cudaMemcpyDeviceToHost, x.s_out);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync (host batch output)");
+            ++k;
+        }
+        if (st == PFB_OK) {
+            e = cudaEventRecord(x.ev_free[b], x.s_out);
+            if (e != cudaSuccess) st = cuda_fail(e, "host batch slot event");
+        }
+    }
+    // nothing may still be writing host memory (or reading the slots) when
+    // the call returns, whatever happened above
+    cudaError_t e1 = cudaEventRecord(x.ev_done, x.s_out);
+    if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(s, x.ev_done, 0);
+    cudaError_t e2 = cudaStreamSynchronize(x.s_in);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    cudaError_t e4 = cudaStreamSynchronize(x.s_out);
+    if (st != PFB_OK) return st;
+    if (e1 != cudaSuccess) return cuda_fail(e1, "host batch completion event");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "host batch copy-in");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "host batch kernels");
+    if (e4 != cudaSuccess) return cuda_fail(e4, "host batch copy-out");
+    // kernel error words of every plan of the batch
+    pfb_status kst = PFB_OK;
+    for (int i = 0; i < n_items; ++i) {
+        pfb_status k = take_kernel_error(reinterpret_cast<Plan *>(items[i].plan)->h_err, "pfb_execute_batch_host");
+        if (kst == PFB_OK) kst = k;
+    }
+    return kst;
 }
 
 extern "C" pfb_status pfb_batch_create(const pfb_batch_item *items, int32_t n_items, pfb_batch_t *out_batch) {

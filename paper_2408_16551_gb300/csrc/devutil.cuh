@@ -182,10 +182,22 @@ __device__ __forceinline__ const void *frame_source(const StreamDesc &d, int64_t
 __device__ __forceinline__ void store_cs(float2 *p, float2 v) { __stcs(p, v); }
 
 // locate the stream owning global work unit u (streams sorted by unit0)
+// Report a failure code into the launch's error word (host-mapped memory: a
+// plain store, made visible to the host before the kernel's completion).
+__device__ __forceinline__ void report_error(int *err, int code) {
+    *reinterpret_cast<volatile int *>(err) = code;
+    __threadfence_system();
+}
+
 __device__ __forceinline__ int find_stream(const LaunchArgs &a, int64_t u) {
-    int i = 0;
-    while (i + 1 < a.nstreams && a.s[i + 1].unit0 <= u) ++i;
-    return i;
+    // last stream whose first unit is <= u (unit0 ascends with the index)
+    int lo = 0, hi = a.nstreams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.s[mid].unit0 <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace pfb

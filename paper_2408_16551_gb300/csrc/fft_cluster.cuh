@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(ClusterCfg<CS, TC>::NT, 1) k_fft_cluster(const
             mbar_wait(smem_u32(&tcbar[0]), (ph1 + 1) & 1);
             mbar_wait(smem_u32(&tcbar[1]), (ph2 + 1) & 1);
         }
-        if (!tc_ok && t == 0) atomicExch(a.err, KERR_TIMEOUT);
+        if (!tc_ok && t == 0) report_error(a.err, KERR_TIMEOUT);
         tc_fence_before();
         __syncthreads();
         if (t < 32) {

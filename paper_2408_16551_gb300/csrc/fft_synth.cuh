@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(SyCfg<P, TT>::NTHREADS, 1) k_synth_ws(const __
         __syncwarp();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
+    if (threadIdx.x == 0 && *abort_flag) report_error(a.err, KERR_TIMEOUT);
 }
 
 }  // namespace pfb

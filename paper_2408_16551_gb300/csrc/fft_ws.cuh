@@ -41,10 +41,6 @@
 
 namespace pfb {
 
-#ifndef PFB_WS_DIF4
-#define PFB_WS_DIF4 1
-#endif
-
 template <int P, int TT, int IN, bool TC = false>
 struct WsCfg {
     static constexpr int NB = P >= 1024 ? 4 : (P >= 512 ? 2 : 1);  // branches per FIR thread
@@ -53,7 +49,7 @@ struct WsCfg {
     // decimation-in-frequency butterfly before handing over; the FFT warps
     // apply its twiddles in their first pass and run four P/4-point
     // transforms per spectrum
-    static constexpr bool DIF4 = PFB_WS_DIF4 && (P == 1024) && !TC;
+    static constexpr bool DIF4 = (P == 1024) && !TC;
     static constexpr int Q = P / 4;                                  // sub-transform length (DIF4)
     static constexpr int SROW = Q + Q / 16 + 8;                      // sub-row stride (float2), 16 banks apart
     static constexpr int NFT = P / NB;                               // FIR threads
@@ -320,14 +316,14 @@ __device__ __forceinline__ void ws_tc_mma_thread(const LaunchArgs &a, WsRange ra
     while (ok && ws_next_segment(a, range, si, sA, sB)) {
         const int64_t nb = (sB - sA + SB - 1) / SB;
         for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
-            if (!mbar_wait(op1, bc & 1)) {
+            if (!mbar_wait(op1, bc & 1, a.wait_ns)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             ws_tc_issue<C>(false, tmem, sA2, sBT, mbar1);
             ++issued1;
-            if (!mbar_wait(op2, bc & 1)) {
+            if (!mbar_wait(op2, bc & 1, a.wait_ns)) {
                 ok = false;
                 break;
             }
@@ -338,8 +334,8 @@ __device__ __forceinline__ void ws_tc_mma_thread(const LaunchArgs &a, WsRange ra
     }
     if (!ok) *abort_flag = 1;
     // everything issued has completed before the CTA frees TMEM
-    if (issued1 && !mbar_wait(mbar1, (issued1 - 1) & 1)) *abort_flag = 1;
-    if (issued2 && !mbar_wait(mbar2, (issued2 - 1) & 1)) *abort_flag = 1;
+    if (issued1 && !mbar_wait(mbar1, (issued1 - 1) & 1, a.wait_ns)) *abort_flag = 1;
+    if (issued2 && !mbar_wait(mbar2, (issued2 - 1) & 1, a.wait_ns)) *abort_flag = 1;
 }
 
 template <class C>
@@ -359,7 +355,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
     // every DFT thread waits; the barrier ORs the failures so all take the same path
     uint32_t ph1 = 0, ph2 = 0;  // completions observed on mbar1 / mbar2
     auto wait_mma = [&](uint32_t bar, uint32_t &ph) {
-        const bool w = mbar_wait(bar, ph & 1);
+        const bool w = mbar_wait(bar, ph & 1, a.wait_ns);
         ++ph;
         const bool fail = named_bar_or<2>(NT, !w);
         tc_fence_after();
@@ -389,7 +385,7 @@ __device__ __forceinline__ void ws_tc_dft(const LaunchArgs &a, WsRange range, ui
     while (ok && ws_next_segment(a, range, si, sA, sB)) {
         const int64_t nb = (sB - sA + SB - 1) / SB;
         for (int64_t qb = 0; qb < nb && ok; ++qb, ++bc) {
-            if (ft == 0) meta[2].nrows = mbar_wait(yfull0 + 8 * (bc & 1), (bc >> 1) & 1) ? 1 : 0;
+            if (ft == 0) meta[2].nrows = mbar_wait(yfull0 + 8 * (bc & 1), (bc >> 1) & 1, a.wait_ns) ? 1 : 0;
             named_bar_sync<1>(NT);
             if (!meta[2].nrows) {
                 *abort_flag = 1;
@@ -574,7 +570,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                         // ---- frame i of the segment from the ring ----
                         const uint32_t slot = pc % NSLOT;
                         // warp-uniform decision: every lane takes the same path
-                        if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * slot, (pc / NSLOT) & 1))) {
+                        if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * slot, (pc / NSLOT) & 1, a.wait_ns))) {
                             *abort_flag = 1;
                             ok = false;
                             break;
@@ -649,7 +645,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                             const int brow = (k + 1) % SB;
                             // new batch: wait until the FFT warps have released this Y buffer
                             if (brow == 0 && bc >= 2 &&
-                                !__all_sync(0xffffffffu, mbar_wait(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1))) {
+                                !__all_sync(0xffffffffu, mbar_wait(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1, a.wait_ns))) {
                                 *abort_flag = 1;
                                 ok = false;
                                 break;
@@ -705,7 +701,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
             for (int64_t q = 0; q < nb && ok; ++q, ++bc) {
                 // one thread waits, the decision is broadcast so that every FFT
                 // thread reaches the same named barriers
-                if (ft == 0) meta[2].nrows = mbar_wait(yfull0 + 8 * (bc & 1), (bc >> 1) & 1) ? 1 : 0;
+                if (ft == 0) meta[2].nrows = mbar_wait(yfull0 + 8 * (bc & 1), (bc >> 1) & 1, a.wait_ns) ? 1 : 0;
                 named_bar_sync<1>(C::NFFTT);
                 if (!meta[2].nrows) {
                     *abort_flag = 1;
@@ -739,7 +735,10 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
         }
         if (warp == C::PRODW && lane == 0) {
             uint32_t pc = 0;
-            bool ok = true;
+            // error-reporting test hook: with FAULT_NO_COPIES the producer
+            // issues no copies at all, so every consumer's bounded wait runs
+            // out, the roles wind down and the error word is set
+            bool ok = TC || a.fault != FAULT_NO_COPIES;
             int si;
             int64_t sA, sB;
             while (ok && ws_next_segment(a, range, si, sA, sB)) {
@@ -748,7 +747,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                 const uint8_t *in = static_cast<const uint8_t *>(d.in);
                 for (int64_t f = sA; f < f_end && ok; ++f, ++pc) {
                     const uint32_t slot = pc % NSLOT;
-                    if (pc >= NSLOT && !mbar_wait(empty0 + 8 * slot, ((pc / NSLOT) + 1) & 1)) {
+                    if (pc >= NSLOT && !mbar_wait(empty0 + 8 * slot, ((pc / NSLOT) + 1) & 1, a.wait_ns)) {
                         *abort_flag = 1;
                         ok = false;
                         break;
@@ -763,7 +762,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
             // drain: every copy issued must have landed before the CTA exits
             const uint32_t first = pc > NSLOT ? pc - NSLOT : 0;
             for (uint32_t q = first; q < pc; ++q) {
-                if (!mbar_wait(full0 + 8 * (q % NSLOT), (q / NSLOT) & 1)) *abort_flag = 1;
+                if (!mbar_wait(full0 + 8 * (q % NSLOT), (q / NSLOT) & 1, a.wait_ns)) *abort_flag = 1;
             }
         }
         __syncwarp();
@@ -776,7 +775,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
             tmem_dealloc(*tmem_slot, kTcCols);
         }
     }
-    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
+    if (threadIdx.x == 0 && *abort_flag) report_error(a.err, KERR_TIMEOUT);
 }
 
 // rows of the launch: one work unit per spectrum

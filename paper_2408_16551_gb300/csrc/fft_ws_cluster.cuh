@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(WcCfg<CS, TT, IN, TC>::NTHREADS, 1)
             tmem_dealloc(*tmem_slot, kTcCols);
         }
     }
-    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
+    if (threadIdx.x == 0 && *abort_flag) report_error(a.err, KERR_TIMEOUT);
 }
 
 }  // namespace pfb

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k_gemm_bf16x3(const __grid_cons
             if (last_commit >= 0) ok = mbar_wait(mdone0 + 8 * (last_commit & 1), (last_commit >> 1) & 1) && ok;
             if (last_copy > last_waited_full)
                 ok = mbar_wait(bfull0 + 8 * (last_copy & 1), (last_copy >> 1) & 1) && ok;
-            if (!ok || *abort_flag) atomicExch(a.err, KERR_TIMEOUT);
+            if (!ok || *abort_flag) report_error(a.err, KERR_TIMEOUT);
         }
         __syncwarp();
         tc_fence_after();

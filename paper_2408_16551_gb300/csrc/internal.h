@@ -57,7 +57,15 @@ struct StreamDesc {
     int32_t T;             // taps per branch
 };
 
-constexpr int kMaxStreamsPerLaunch = 32;
+constexpr int kMaxStreamsPerLaunch = 64;
+constexpr int kMaxOversampling = 32;          // most spectra per frame (P / hop)
+constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // bound of every device-side wait
+
+// Fault modes of the error-reporting test hook (pfb_plan_set_fault).
+enum : int32_t {
+    FAULT_NONE = 0,
+    FAULT_NO_COPIES = 1,  // the producer issues no input copies: every consumer wait runs out
+};
 
 struct LaunchArgs {
     StreamDesc s[kMaxStreamsPerLaunch];
@@ -66,7 +74,10 @@ struct LaunchArgs {
     int64_t nunits;         // total work units in this launch
     const float2 *tw;       // FFT twiddle table for the family's P
     const void *aux;        // family-specific table (DFT matrix for GEMM paths)
-    int *err;               // device error word
+    int *err;               // error word (host-mapped memory): KERR_* of a failed launch
+    uint64_t wait_ns;       // bound of the kernel's device-side waits (%globaltimer ns)
+    int32_t fault;          // FAULT_* test hook (0 in normal use)
+    int32_t pad_;
 };
 
 // ---------------------------------------------------------------------------
@@ -103,7 +114,10 @@ struct Plan {
     void *d_dft = nullptr;          // DFT matrix (GEMM families)
     void *d_tcf = nullptr;          // factored split-bf16 DFT: 32-point matrix hi/lo + twiddles
     size_t dft_bytes = 0;
-    int *d_err = nullptr;           // device error word
+    int *h_err = nullptr;           // error word in mapped, pinned host memory (written by kernels)
+    int *d_err = nullptr;           // its device address
+    uint64_t wait_ns = kDefaultWaitNs;  // device-side wait bound of the plan's launches
+    int32_t fault = 0;              // FAULT_* test hook
     // host staging for pfb_execute_host
     std::mutex stage_mu;
     void *d_stage_in = nullptr, *d_stage_out = nullptr;
@@ -124,8 +138,23 @@ bool is_pow2(int64_t v);
 int ilog2(int64_t v);
 
 // Launch one kernel of the plan's family over the given streams (all with
-// the plan's P, T, dtype).  `descs` unit0 fields are filled in here.
-pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream);
+// the plan's P, T, dtype).  `descs` unit0 fields are filled in here.  The
+// kernels report failures into `err` (device address of a host-mapped word;
+// nullptr = the plan's own word).
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err = nullptr);
+
+// Read and clear a host-mapped error word: PFB_OK, or the status a kernel's
+// KERR_* code maps to (KERR_TIMEOUT -> PFB_ERR_TIMEOUT, others ->
+// PFB_ERR_INTERNAL), with the message set.
+pfb_status take_kernel_error(int *h_err, const char *what);
+
+// Resolve (and cache) the device address of the static staging area of
+// pfb_execute_host_noalloc on `device` (current); loads its module there.
+pfb_status noalloc_prepare(int device);
+
+// Mapped, pinned host words the kernels write their error codes to.
+pfb_status alloc_error_words(int n, int **h_err, int **d_err);
+void free_error_words(int *h_err);
 
 // Family-specific launchers (defined in their .cu files).
 pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &args, cudaStream_t stream);

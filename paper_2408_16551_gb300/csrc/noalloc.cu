@@ -26,8 +26,22 @@ static_assert(PFB_NOALLOC_SCRATCH_BYTES % 256 == 0, "staging area must be a mult
 // name is only a host-side handle, so the address is looked up once per
 // device (with that device current) and cached.
 constexpr int kMaxDevices = 64;
+static pfb_status scratch_address(int device, void **out);
 static std::mutex g_scratch_mu;
 static void *g_scratch_ptr[kMaxDevices] = {};
+
+}  // namespace pfb
+
+// Called by pfb_plan_create with the plan's device current: resolving the
+// address loads this translation unit's module on that device (under lazy
+// module loading that is when the static area is reserved), so the first
+// pfb_execute_host_noalloc call neither loads a module nor reserves memory.
+pfb_status pfb::noalloc_prepare(int device) {
+    void *p = nullptr;
+    return scratch_address(device, &p);
+}
+
+namespace pfb {
 
 static pfb_status scratch_address(int device, void **out) {
     if (device < 0 || device >= kMaxDevices) return fail(PFB_ERR_INVALID, "device ordinal out of range");
@@ -108,6 +122,8 @@ extern "C" pfb_status pfb_execute_host_noalloc(pfb_plan_t plan, const void *host
         e = cudaMemcpyAsync(host_out, dout, (size_t)out_bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "staging area to host copy");
+        // the kernel's error word (host-mapped, allocated with the plan)
+        if (st == PFB_OK) st = take_kernel_error(p.h_err, "pfb_execute_host_noalloc");
     } while (0);
     if (prev >= 0 && prev != p.device) cudaSetDevice(prev);
     return st;

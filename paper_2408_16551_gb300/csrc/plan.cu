@@ -154,7 +154,7 @@ static pfb_status validate(const pfb_plan_desc *d) {
     if (d->hop != 0 && d->hop != d->P) {
         const int esize = d->in_dtype == PFB_IN_R32 ? 4 : d->in_dtype == PFB_IN_C64 ? 8 : 2;
         if (d->hop < 1 || d->hop > d->P || d->P % d->hop != 0) return fail(PFB_ERR_INVALID, "hop must divide P");
-        if (d->P / d->hop > kMaxStreamsPerLaunch) return fail(PFB_ERR_INVALID, "oversampling P/hop above 32");
+        if (d->P / d->hop > kMaxOversampling) return fail(PFB_ERR_INVALID, "oversampling P/hop above 32");
         if ((d->hop * esize) % 16 != 0)
             return fail(PFB_ERR_INVALID, "hop * bytes per sample must be a multiple of 16");
     }
@@ -174,7 +174,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->d_tw32);
     cudaFree(p->d_dft);
     cudaFree(p->d_tcf);
-    cudaFree(p->d_err);
+    free_error_words(p->h_err);
     if (p->s_copy_in) cudaStreamDestroy(p->s_copy_in);
     if (p->s_copy_out) cudaStreamDestroy(p->s_copy_out);
     for (cudaEvent_t e : p->ev_pipe)
@@ -210,8 +210,10 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     p->variant = default_variant(*p);
 
     const int P = p->P, T = p->T, L = P * T;
-    PFB_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
-    PFB_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+    {
+        pfb_status est = alloc_error_words(1, &p->h_err, &p->d_err);
+        if (est != PFB_OK) return est;
+    }
     PFB_CUDA_TRY(cudaMalloc(&p->d_h64, sizeof(double) * L));
     if (desc->window == PFB_WIN_USER) {
         PFB_CUDA_TRY(cudaMemcpy(p->d_h64, desc->user_taps_host, sizeof(double) * L, cudaMemcpyHostToDevice));
@@ -244,6 +246,12 @@ static pfb_status create_impl(const pfb_plan_desc *desc, Plan *p) {
     }
     PFB_CUDA_TRY(cudaGetLastError());
     PFB_CUDA_TRY(cudaDeviceSynchronize());
+    {
+        // the static staging area of pfb_execute_host_noalloc is reserved and
+        // its address cached now, not inside that entry point's first call
+        pfb_status nst = noalloc_prepare(p->device);
+        if (nst != PFB_OK) return nst;
+    }
     {
         pfb_status pst = prepare_family(*p);
         if (pst != PFB_OK && pst != PFB_ERR_UNSUPPORTED) return pst;

@@ -134,6 +134,7 @@ struct PStream {
 struct Batch {
     std::vector<Request *> reqs;
     cudaEvent_t done = nullptr;
+    int err_idx = -1;                // this batch's kernel error word (server pool)
     int cs = 0;
     Clock::time_point t_launch;
     bool device_done = false;
@@ -148,6 +149,10 @@ struct Server {
     bool stop = false;
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> free_events;
+    // kernel error words, one per batch in flight (mapped, pinned host memory)
+    static constexpr int kErrWords = 256;
+    int *h_err = nullptr, *d_err = nullptr;
+    std::vector<int> free_err;
     std::map<int64_t, std::unique_ptr<PStream>> streams;
     std::map<int64_t, std::unique_ptr<Request>> tickets;
     std::deque<Request *> queue;             // submitted, not launched (submission order)
@@ -315,8 +320,15 @@ static void launch_batch(Server &s) {
         ps.cur ^= 1;
         ps.state_frames = keep;
     }
+    if (s.free_err.empty()) st = fail(PFB_ERR_INTERNAL, "no free kernel error word");
+    else {
+        b->err_idx = s.free_err.back();
+        s.free_err.pop_back();
+        s.h_err[b->err_idx] = KERR_NONE;
+    }
     for (auto &g : groups) {
-        if (st == PFB_OK) st = launch_family(*g.first, g.second.data(), (int)g.second.size(), cs);
+        if (st == PFB_OK)
+            st = launch_family(*g.first, g.second.data(), (int)g.second.size(), cs, s.d_err + b->err_idx);
     }
     if (st == PFB_OK) st = launch_state_updates(ups, cs);
     b->done = get_event(s);
@@ -324,6 +336,12 @@ static void launch_batch(Server &s) {
     if (st != PFB_OK) {
         for (Request *r : go) finish(s, *r, st);
         if (b->done) s.free_events.push_back(b->done);
+        if (b->err_idx >= 0) {
+            // a launch may have gone out before the failure: the word is
+            // reused only once the device has finished that launch
+            cudaStreamSynchronize(cs);
+            s.free_err.push_back(b->err_idx);
+        }
         return;
     }
     for (int64_t sid : order) {
@@ -355,6 +373,12 @@ static void poll_inflight(Server &s) {
             cudaError_t q = cudaEventQuery(b.done);
             if (q == cudaSuccess) {
                 b.device_done = true;
+                // a kernel of the batch whose bounded wait ran out wrote its
+                // error word: the batch's spectra are not valid
+                const pfb_status kst = take_kernel_error(s.h_err + b.err_idx, "batch kernel");
+                if (kst != PFB_OK)
+                    for (Request *r : b.reqs)
+                        if (r->status == PFB_PENDING && !r->lost) finish(s, *r, kst);
             } else if (q != cudaErrorNotReady) {
                 cudaGetLastError();
                 b.device_done = true;
@@ -384,6 +408,7 @@ static void poll_inflight(Server &s) {
             for (auto &kv : s.streams)
                 if (kv.second->last_event == b.done) kv.second->last_event = nullptr;
             s.free_events.push_back(b.done);
+            if (b.err_idx >= 0) s.free_err.push_back(b.err_idx);
             s.batches[i] = std::move(s.batches.back());
             s.batches.pop_back();
         } else {
@@ -449,6 +474,16 @@ extern "C" pfb_status pfb_server_create(const pfb_server_desc *desc, pfb_server_
         }
         s->pool.push_back(cs);
     }
+    {
+        pfb_status est = alloc_error_words(Server::kErrWords, &s->h_err, &s->d_err);
+        if (est != PFB_OK) {
+            for (auto p : s->pool) cudaStreamDestroy(p);
+            cudaSetDevice(prev);
+            delete s;
+            return est;
+        }
+        for (int i = Server::kErrWords - 1; i >= 0; --i) s->free_err.push_back(i);
+    }
     cudaSetDevice(prev);
     s->worker = std::thread(worker_loop, s);
     *out_server = reinterpret_cast<pfb_server_t>(s);
@@ -486,6 +521,7 @@ extern "C" pfb_status pfb_server_destroy(pfb_server_t server) {
         cudaFree(kv.second->state[1]);
     }
     for (auto cs : s->pool) cudaStreamDestroy(cs);
+    free_error_words(s->h_err);
     cudaSetDevice(prev);
     delete s;
     return result;

@@ -1,7 +1,8 @@
 """The benchmark's reference arm on the CPU: one JSON line with the keys of the
-benchmark contract, timed on the FP64 oracle over bounded samples of the c2
-workload, and sample windows that stay inside the workload however many steps
-are asked for."""
+benchmark contract, timed on the FP64 oracle over bounded samples of the c3
+workload (the headline), and sample windows that stay inside the workload
+however many steps are asked for.  Also the paper-style NumPy FP32 baseline
+the benchmark reports beside the oracle: it must compute the channeliser."""
 
 import json
 import os
@@ -28,7 +29,7 @@ def test_reference_arm_line():
     assert d["impl"] == "reference"
     assert d["steps"] == 3 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"].startswith("c2")
+    assert d["config"]["workload"].startswith("c3")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
@@ -45,6 +46,23 @@ def test_reference_arm_other_ranks_print_nothing():
 
 
 def test_reference_arm_long_runs_wrap():
-    # 300 samples of 64 spectra exceed the 16369 spectra of the workload
-    d = _run("--steps", "300", "--warmup", "3")
-    assert d["steps"] == 300 and d["value"] > 0
+    # 100 samples of 16 spectra run past the 241 spectra of a stream
+    d = _run("--steps", "100", "--warmup", "3")
+    assert d["steps"] == 100 and d["value"] > 0
+
+
+def test_numpy_paper_style_baseline_is_the_channeliser():
+    """bench.numpy_pfb_f32 (the CPU comparison program) against the FP64
+    oracle: FP32 accuracy on a ragged c3-like stream, every spectrum."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2408_16551_gb300 import synth
+    P, T = 512, 16
+    x = synth.small_stream(P, T, P * 80 + 13, seed=3, window=synth.WIN_BLACKMAN).generate()
+    h = oracle.prototype(P, T, oracle.WIN_BLACKMAN)
+    got = bench.numpy_pfb_f32(x, P, T, h.astype(np.float32))
+    ref = oracle.pfb(oracle.dequant(x, oracle.IN_C64), P, T, h)
+    assert got.shape == ref.shape and got.dtype == np.complex64
+    assert oracle.rel_l2(got, ref) < 2e-6

@@ -10,6 +10,7 @@ import paper_2408_16551_gb300 as pkg
 from paper_2408_16551_gb300 import synth
 
 from gpu_common import TOL_BF16X3, TOL_MAX_BF16X3, assert_close, reference, to_device
+from split_models import factored_dft_model, split_bf16x3_model
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +77,7 @@ def test_gemm_bf16x3_matches_split_model(P, T):
     plan, x, got = _run_variant(0, P, T, synth.IN_C64, n, seed=9)
     h = oracle.prototype(P, T, oracle.WIN_HANN)
     y = oracle.fir(oracle.dequant(x, oracle.IN_C64), P, T, h)
-    model = oracle.split_bf16x3_model(y.astype(np.complex64), P)
+    model = split_bf16x3_model(y.astype(np.complex64), P)
     exact = oracle.dft(y)
     e_model = oracle.rel_l2(got, model)
     e_exact = oracle.rel_l2(got, exact)
@@ -165,7 +166,7 @@ def test_gemm_bf16x3_factored_matches_model():
     plan, x, got = _run_variant(1, P, T, synth.IN_C64, n, seed=19)
     h = oracle.prototype(P, T, oracle.WIN_HANN)
     y = oracle.fir(oracle.dequant(x, oracle.IN_C64), P, T, h)
-    model = oracle.factored_dft_model(y.astype(np.complex64), 32, 32)
+    model = factored_dft_model(y.astype(np.complex64), 32, 32)
     e_model = oracle.rel_l2(got, model)
     e_exact = oracle.rel_l2(got, oracle.dft(y))
     assert e_model < 2e-6, e_model

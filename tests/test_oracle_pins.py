@@ -316,60 +316,6 @@ def test_pins_reject_positive_exponent():
 
 
 # --------------------------------------------------------------------------
-# split-bf16 model helpers
-# --------------------------------------------------------------------------
-
-def test_bf16_round_matches_torch():
-    torch = pytest.importorskip("torch")
-    rng = np.random.default_rng(21)
-    v = (rng.standard_normal(20000) * 10.0 ** rng.uniform(-6, 6, 20000)).astype(np.float32)
-    v = np.concatenate([v, np.float32([1.0, -1.0, 1.00390625, 1.005859375, 0.0])])  # exact and halfway cases
-    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
-    got = oracle.bf16_round(v.astype(np.float64))
-    assert np.array_equal(got, ref)
-
-
-@pytest.mark.parametrize("P", [4, 16, 64])
-def test_dft_block_matrix_reproduces_dft(P):
-    rng = np.random.default_rng(P)
-    y = rng.standard_normal((5, P)) + 1j * rng.standard_normal((5, P))
-    A = np.empty((5, 2 * P)); A[:, 0::2] = y.real; A[:, 1::2] = y.imag
-    Xr = A @ oracle.dft_block_matrix(P)
-    X = Xr[:, 0::2] + 1j * Xr[:, 1::2]
-    assert np.max(np.abs(X - np.fft.fft(y, axis=1))) < 1e-12
-
-
-def test_split_model_error_is_small_but_nonzero():
-    P = 64
-    rng = np.random.default_rng(3)
-    y = (rng.standard_normal((8, P)) + 1j * rng.standard_normal((8, P))).astype(np.complex64)
-    X = oracle.split_bf16x3_model(y, P)
-    ref = np.fft.fft(y.astype(np.complex128), axis=1)
-    e = oracle.rel_l2(X, ref)
-    assert 1e-7 < e < 1e-5
-
-
-@pytest.mark.parametrize("P1,P2", [(4, 4), (2, 8), (8, 2), (32, 32), (16, 4)])
-def test_factored_dft_model_unsplit_is_the_dft(P1, P2):
-    """Four-step factoring (p = P2 n1 + n2, k = k1 + P1 k2, twiddle w_P^(n2 k1))
-    against numpy.fft: a wrong index role, twiddle sign or output order fails."""
-    rng = np.random.default_rng(P1 * 100 + P2)
-    y = rng.standard_normal((6, P1 * P2)) + 1j * rng.standard_normal((6, P1 * P2))
-    ref = np.fft.fft(y, axis=1)
-    got = oracle.factored_dft_model(y, P1, P2, split=False)
-    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
-
-
-def test_factored_dft_model_split_error_is_bounded():
-    """Split-bf16 four-step model at P = 32 x 32: error at the split level (two
-    products of hi/lo operands), inside the 1e-5 bound, and not zero."""
-    rng = np.random.default_rng(31)
-    y = (rng.standard_normal((6, 1024)) + 1j * rng.standard_normal((6, 1024))).astype(np.complex64)
-    e = oracle.rel_l2(oracle.factored_dft_model(y, 32, 32), np.fft.fft(y.astype(np.complex128), axis=1))
-    assert 1e-7 < e < 1e-5
-
-
-# --------------------------------------------------------------------------
 # oversampled channeliser (hop D < P) and the convolution tap order
 # --------------------------------------------------------------------------
 
