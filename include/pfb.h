@@ -149,7 +149,7 @@ PFB_API pfb_status pfb_plan_status(pfb_plan_t plan);
  * variant 5) issue no input copies, so every consumer's bounded wait runs
  * out after wait_ns nanoseconds and the launch reports PFB_ERR_TIMEOUT; no
  * memory is touched and no GPU fault is provoked.  mode 0 restores normal
- * operation.  wait_ns (0 = the default of 1 s, at most 10 s) bounds the
+ * operation.  wait_ns (0 = the default of 1 s, at most 4 s) bounds the
  * device-side waits of the plan's launches in either mode; kernels other
  * than that one ignore the mode and keep the default bound.
  * Errors: PFB_ERR_INVALID for an unknown mode or wait_ns out of range. */
@@ -342,6 +342,23 @@ PFB_API int64_t pfb_stream_next_spectra(pfb_server_t server, int64_t stream_id, 
 PFB_API pfb_status pfb_submit(pfb_server_t server, int64_t stream_id, const void *d_chunk,
                       int64_t n_samples, void *d_out, int64_t out_cap_spectra,
                       int64_t *out_ticket);
+
+/* n_chunks consecutive chunks of one stream in one call, the same as
+ * n_chunks pfb_submit calls in order: chunk i is samples_per_chunk samples
+ * (a multiple of P) at d_chunks + i * samples_per_chunk samples; its spectra
+ * go to d_out right after those of chunks 0..i-1 (out_cap_spectra rows in
+ * all).  out_tickets receives n_chunks tickets.  On an error the chunks
+ * before the failing one stay submitted (their tickets are set, the rest are
+ * 0) and the error is returned. */
+PFB_API pfb_status pfb_submit_chunks(pfb_server_t server, int64_t stream_id, const void *d_chunks, int32_t n_chunks,
+                                     int64_t samples_per_chunk, void *d_out, int64_t out_cap_spectra,
+                                     int64_t *out_tickets);
+
+/* The server's timestamps of a ticket, in seconds of the library's steady
+ * clock (CLOCK_MONOTONIC on Linux): when pfb_submit accepted it and when the
+ * server saw it finish (its batch's completion event, polled every few
+ * microseconds by the server thread); *t_done_s = 0 while it is pending. */
+PFB_API pfb_status pfb_ticket_times(pfb_server_t server, int64_t ticket, double *t_submit_s, double *t_done_s);
 
 /* PFB_PENDING while queued or running, PFB_OK once the output is complete,
  * or the request's error.  Never blocks.  A finished ticket can be polled

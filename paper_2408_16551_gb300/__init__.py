@@ -41,7 +41,7 @@ EXPORTED = [
     "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
     "pfb_execute_host_noalloc", "pfb_stream_state_size", "pfb_stream_state_export", "pfb_stream_state_import",
     "pfb_synth_out_samples", "pfb_synthesize", "pfb_plan_status", "pfb_plan_set_fault",
-    "pfb_execute_batch_host",
+    "pfb_execute_batch_host", "pfb_submit_chunks", "pfb_ticket_times",
 ]
 
 
@@ -123,6 +123,8 @@ def lib() -> ctypes.CDLL:
             "pfb_stream_next_spectra": (i64, [vp, i64, i64]),
             "pfb_submit": (st, [vp, i64, vp, i64, vp, i64, ctypes.POINTER(i64)]),
             "pfb_poll": (st, [vp, i64]),
+            "pfb_submit_chunks": (st, [vp, i64, vp, i32, i64, vp, i64, ctypes.POINTER(i64)]),
+            "pfb_ticket_times": (st, [vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "pfb_wait": (st, [vp, i64, i32]),
             "pfb_server_get_stats": (st, [vp, ctypes.POINTER(pfb_server_stats)]),
             "pfb_status_string": (ctypes.c_char_p, [st]),
@@ -400,6 +402,23 @@ class Server:
         _check(lib().pfb_submit(self.handle, sid, ctypes.c_void_p(chunk.data_ptr()), n_samples, out_ptr, cap,
                                 ctypes.byref(t)), "pfb_submit")
         return t.value
+
+    def submit_chunks(self, sid: int, chunks, n_chunks: int, samples_per_chunk: int, out) -> list:
+        """pfb_submit_chunks: n_chunks consecutive chunks of one device buffer in
+        one call; returns their tickets."""
+        t = (ctypes.c_int64 * n_chunks)()
+        out_ptr = ctypes.c_void_p(out.data_ptr()) if out is not None and out.numel() else None
+        cap = out.shape[0] if out is not None else 0
+        _check(lib().pfb_submit_chunks(self.handle, sid, ctypes.c_void_p(chunks.data_ptr()), n_chunks,
+                                       samples_per_chunk, out_ptr, cap, t), "pfb_submit_chunks")
+        return list(t)
+
+    def ticket_times(self, ticket: int):
+        """pfb_ticket_times: (submitted, finished) in seconds of the steady clock
+        (time.monotonic() on Linux); finished is 0.0 while pending."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().pfb_ticket_times(self.handle, ticket, ctypes.byref(a), ctypes.byref(b)), "pfb_ticket_times")
+        return a.value, b.value
 
     def poll(self, ticket: int) -> int:
         return int(lib().pfb_poll(self.handle, ticket))

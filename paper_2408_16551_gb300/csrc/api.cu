@@ -242,7 +242,7 @@ extern "C" pfb_status pfb_plan_set_fault(pfb_plan_t plan, int32_t mode, int64_t 
     clear_error();
     if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
     if (mode != FAULT_NONE && mode != FAULT_NO_COPIES) return fail(PFB_ERR_INVALID, "unknown fault mode");
-    if (wait_ns < 0 || wait_ns > 10ll * (int64_t)kDefaultWaitNs) return fail(PFB_ERR_INVALID, "wait_ns outside [0, 10 s]");
+    if (wait_ns < 0 || wait_ns > 4ll * (int64_t)kDefaultWaitNs) return fail(PFB_ERR_INVALID, "wait_ns outside [0, 4 s]");
     Plan &p = *reinterpret_cast<Plan *>(plan);
     p.fault = mode;
     p.wait_ns = wait_ns == 0 ? kDefaultWaitNs : (uint64_t)wait_ns;

@@ -72,7 +72,8 @@ int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) {
 // elements at element offset (ng*8 + kg)*64, row r at +8r, element e at +e
 // (leading-dimension byte offset 128 B along K, stride 1024 B along N).
 // ---------------------------------------------------------------------------
-__global__ void gen_dft_bf16x3_kernel(__nv_bfloat16 *Bhi, __nv_bfloat16 *Blo, int P) {
+// conj = 1: the conjugate matrix (exponent +2 pi i pk/P), for the inverse DFT
+__global__ void gen_dft_bf16x3_kernel(__nv_bfloat16 *Bhi, __nv_bfloat16 *Blo, int P, int conj) {
     const int64_t total = (int64_t)2 * P * 2 * P;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= total) return;
@@ -88,6 +89,7 @@ __global__ void gen_dft_bf16x3_kernel(__nv_bfloat16 *Bhi, __nv_bfloat16 *Blo, in
     const int64_t ex = ((int64_t)p * k) % P;
     double s, c;
     sincospi(2.0 * (double)ex / (double)P, &s, &c);
+    if (conj) s = -s;
     double v;
     if (csel == dsel) v = c;
     else if (csel == 1) v = s;   // B[2p+1][2k]
@@ -98,16 +100,21 @@ __global__ void gen_dft_bf16x3_kernel(__nv_bfloat16 *Bhi, __nv_bfloat16 *Blo, in
     Blo[i] = lo;
 }
 
-pfb_status build_gemm_bf16x3_table(Plan &plan) {
+static pfb_status build_table(Plan &plan, int conj) {
     const int64_t n = (int64_t)2 * plan.P * 2 * plan.P;
     plan.dft_bytes = 2 * n * sizeof(__nv_bfloat16);
     PFB_CUDA_TRY(cudaMalloc(&plan.d_dft, plan.dft_bytes));
     __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(plan.d_dft);
-    gen_dft_bf16x3_kernel<<<(unsigned)((n + 255) / 256), 256>>>(hi, hi + n, plan.P);
+    gen_dft_bf16x3_kernel<<<(unsigned)((n + 255) / 256), 256>>>(hi, hi + n, plan.P, conj);
     g_launches++;
     PFB_CUDA_TRY(cudaGetLastError());
     return PFB_OK;
 }
+
+pfb_status build_gemm_bf16x3_table(Plan &plan) { return build_table(plan, 0); }
+
+// the conjugate DFT matrix, for the synthesis bank's inverse DFT
+pfb_status build_gemm_bf16x3_table_conj(Plan &plan) { return build_table(plan, 1); }
 
 pfb_status build_gemm_f32_table(Plan &plan);
 

@@ -107,7 +107,7 @@ struct Plan {
     // device tables (owned)
     double *d_h64 = nullptr;        // FP64 prototype [P*T]
     float *d_taps = nullptr;        // fp32 taps [T][P]
-    float *d_taps_pad = nullptr;    // fp32 taps front-padded [TT][P] (fast FFT family)
+    float *d_taps_pad = nullptr;    // fp32 taps zero-extended to [TT][P] (rows T..TT-1 zero)
     float2 *d_tw = nullptr;         // FFT twiddles (layout per family; radix-16 pass list)
     float2 *d_tw32 = nullptr;       // radix-32 pass list twiddles (fast FFT family)
     float2 *d_tw_r2 = nullptr;      // radix-2 table w^r, r < P/2 (generic family)
@@ -118,6 +118,11 @@ struct Plan {
     int *d_err = nullptr;           // its device address
     uint64_t wait_ns = kDefaultWaitNs;  // device-side wait bound of the plan's launches
     int32_t fault = 0;              // FAULT_* test hook
+    // synthesis routes other than the fused kernel: the inverse-DFT buffer
+    // y~ [S][P] and (split-bf16 plans) the internal one-tap inverse plan
+    void *d_synth_y = nullptr;
+    size_t synth_y_bytes = 0;
+    Plan *inv = nullptr;
     // host staging for pfb_execute_host
     std::mutex stage_mu;
     void *d_stage_in = nullptr, *d_stage_out = nullptr;
@@ -176,6 +181,11 @@ bool fft_fast_supported(int P, int T);
 int fft_fast_tt(int T);
 int family_variants(const Plan &plan);        // number of variants the autotuner may pick from
 int default_variant(const Plan &plan);
+
+// Synthesis routes (synth_generic.cu): any P, T, path at hop P
+bool synth_generic_supported(const Plan &p);
+pfb_status launch_synth_generic(Plan &p, const float2 *X, int64_t S, float2 *xh, cudaStream_t stream);
+void free_inverse_plan(Plan &p);
 
 // Table generators (plan.cu)
 pfb_status build_fft_fast_twiddles(Plan &plan);

@@ -181,6 +181,8 @@ static void free_plan(Plan *p) {
         if (e) cudaEventDestroy(e);
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
+    cudaFree(p->d_synth_y);
+    free_inverse_plan(*p);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
 }

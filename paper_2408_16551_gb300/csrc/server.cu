@@ -673,6 +673,51 @@ extern "C" pfb_status pfb_poll(pfb_server_t server, int64_t ticket) {
     return it->second->status;
 }
 
+extern "C" pfb_status pfb_submit_chunks(pfb_server_t server, int64_t stream_id, const void *d_chunks,
+                                        int32_t n_chunks, int64_t samples_per_chunk, void *d_out,
+                                        int64_t out_cap_spectra, int64_t *out_tickets) {
+    clear_error();
+    if (!server || !out_tickets) return fail(PFB_ERR_INVALID, "NULL argument");
+    if (n_chunks < 1) return fail(PFB_ERR_INVALID, "n_chunks must be >= 1");
+    for (int32_t i = 0; i < n_chunks; ++i) out_tickets[i] = 0;
+    Server &s = *reinterpret_cast<Server *>(server);
+    int64_t esize = 0, P = 0;
+    {
+        std::lock_guard<std::mutex> lk(s.mu);
+        auto it = s.streams.find(stream_id);
+        if (it == s.streams.end() || it->second->closing) return fail(PFB_ERR_INVALID, "unknown stream");
+        esize = it->second->plan->esize;
+        P = it->second->plan->P;
+    }
+    const char *in = static_cast<const char *>(d_chunks);
+    float2 *out = static_cast<float2 *>(d_out);
+    int64_t row = 0;
+    for (int32_t i = 0; i < n_chunks; ++i) {
+        const int64_t S = pfb_stream_next_spectra(server, stream_id, samples_per_chunk);
+        if (S < 0) return fail(PFB_ERR_INVALID, "unknown stream");
+        if (row + S > out_cap_spectra) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
+        pfb_status st = pfb_submit(server, stream_id, in + (int64_t)i * samples_per_chunk * esize, samples_per_chunk,
+                                   S > 0 ? static_cast<void *>(out + row * P) : nullptr, S, &out_tickets[i]);
+        if (st != PFB_OK) return st;
+        row += S;
+    }
+    return PFB_OK;
+}
+
+extern "C" pfb_status pfb_ticket_times(pfb_server_t server, int64_t ticket, double *t_submit_s, double *t_done_s) {
+    clear_error();
+    if (!server || !t_submit_s || !t_done_s) return fail(PFB_ERR_INVALID, "NULL argument");
+    Server &s = *reinterpret_cast<Server *>(server);
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.tickets.find(ticket);
+    if (it == s.tickets.end()) return fail(PFB_ERR_INVALID, "unknown ticket");
+    const Request &r = *it->second;
+    auto secs = [](Clock::time_point tp) { return std::chrono::duration<double>(tp.time_since_epoch()).count(); };
+    *t_submit_s = secs(r.t_submit);
+    *t_done_s = r.status == PFB_PENDING ? 0.0 : secs(r.t_done);
+    return PFB_OK;
+}
+
 extern "C" pfb_status pfb_wait(pfb_server_t server, int64_t ticket, int32_t timeout_ms) {
     clear_error();
     if (!server) return fail(PFB_ERR_INVALID, "server is NULL");

@@ -62,16 +62,26 @@ extern "C" pfb_status pfb_synthesize(pfb_plan_t plan, const void *d_spectra, int
                                      int64_t out_cap_samples, void *cuda_stream) {
     clear_error();
     if (!plan) return fail(PFB_ERR_INVALID, "plan is NULL");
-    const Plan &p = *reinterpret_cast<Plan *>(plan);
+    Plan &p = *reinterpret_cast<Plan *>(plan);
     if (n_spectra < 0) return fail(PFB_ERR_INVALID, "n_spectra < 0");
     if (n_spectra == 0) return PFB_OK;
-    if (!synth_supported(p))
-        return fail(PFB_ERR_UNSUPPORTED, "synthesis needs an FFT-path plan with P in {512, 1024}, T <= 16, hop P");
+    if (!synth_supported(p) && !synth_generic_supported(p))
+        return fail(PFB_ERR_UNSUPPORTED, p.R != 1 ? "synthesis needs a critically sampled plan (hop P)"
+                                                  : "split-bf16 synthesis needs P >= 128");
     if (!d_spectra || !d_out) return fail(PFB_ERR_INVALID, "NULL buffer with spectra to synthesise");
     if ((reinterpret_cast<uintptr_t>(d_spectra) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 15u))
         return fail(PFB_ERR_INVALID, "buffers must be 16-byte aligned");
     const int64_t frames = n_spectra + p.T - 1;
     if (out_cap_samples < frames * p.P) return fail(PFB_ERR_INVALID, "out_cap_samples smaller than the output");
+    if (!synth_supported(p)) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != p.device) cudaSetDevice(p.device);
+        pfb_status st = launch_synth_generic(p, static_cast<const float2 *>(d_spectra), n_spectra,
+                                             static_cast<float2 *>(d_out), static_cast<cudaStream_t>(cuda_stream));
+        if (prev >= 0 && prev != p.device) cudaSetDevice(prev);
+        return st;
+    }
     LaunchArgs a;
     std::memset(&a, 0, sizeof(a));
     StreamDesc &d = a.s[0];
@@ -87,6 +97,7 @@ extern "C" pfb_status pfb_synthesize(pfb_plan_t plan, const void *d_spectra, int
     a.nunits = frames;
     a.aux = p.d_tw_r2;
     a.err = p.d_err;
+    a.wait_ns = p.wait_ns;
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p.device) cudaSetDevice(p.device);

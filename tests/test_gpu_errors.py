@@ -110,7 +110,7 @@ def test_timeout_fails_the_server_request_and_the_stream_continues():
 
 def test_set_fault_rejects_bad_arguments():
     plan = _plan()
-    for mode, ns in ((2, 0), (-1, 0), (1, -5), (0, 11_000_000_000)):
+    for mode, ns in ((2, 0), (-1, 0), (1, -5), (0, 5_000_000_000)):
         with pytest.raises(pkg.PFBError) as e:
             plan.set_fault(mode, ns)
         assert e.value.status == pkg.PFB_ERR_INVALID

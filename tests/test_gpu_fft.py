@@ -296,35 +296,41 @@ WS_CLUSTER = [(4096, 16, synth.IN_C64, 43), (2048, 16, synth.IN_CI8, 43), (4096,
 
 @pytest.mark.parametrize("P,T,dt,S", WS_CLUSTER)
 def test_cluster_variants_match_oracle(P, T, dt, S):
-    """P = 2048 / 4096 on a CTA cluster: variant 0 (synchronous) and variant 1
-    (warp-specialised, TMA ring, cross-CTA mbarriers) against the oracle, and
-    variant 1 bitwise reproducible."""
+    """P = 2048 / 4096 on a CTA cluster: variant 0 (synchronous), variant 1
+    (warp-specialised, cross-CTA step in the FFT warps) and variant 2
+    (warp-specialised, one exchange from the FIR warps' radix-4 step to the
+    receiving FFT warps' radix-CS step) against the oracle; every
+    warp-specialised variant is bitwise reproducible."""
     import torch
     n = P * (S + T - 1) + 5
     x = synth.small_stream(P, T, n, in_dtype=dt, seed=P + S).generate()
     ref = reference(x, dt, P, T, synth.WIN_BLACKMAN)
     plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_BLACKMAN)
-    assert plan.num_variants == 2 and plan.variant == 1
+    assert plan.num_variants == 3 and plan.variant == 2
     xd = to_device(x)
-    outs = []
-    for v in (0, 1):
+    outs = {}
+    for v in (0, 1, 2):
         plan.variant = v
         X = plan.execute(xd)
         torch.cuda.synchronize()
-        outs.append(X.cpu().numpy())
-        assert_close(outs[-1], ref, what=f"cluster variant {v} P={P} T={T} dt={dt} S={S}")
-    for _ in range(4):  # a ring slot refilled too early shows up as a run of wrong spectra
-        again = plan.execute(xd).cpu().numpy()
-        assert np.array_equal(again, outs[1])
+        outs[v] = X.cpu().numpy()
+        assert plan.status() == pkg.PFB_OK
+        assert_close(outs[v], ref, what=f"cluster variant {v} P={P} T={T} dt={dt} S={S}")
+    for v in (1, 2):
+        plan.variant = v
+        for _ in range(3):  # a ring or receive slot reused too early shows up as wrong spectra
+            again = plan.execute(xd).cpu().numpy()
+            assert np.array_equal(again, outs[v]), v
 
 
-def test_cluster_ws_batch_equals_single():
+@pytest.mark.parametrize("variant", [1, 2])
+def test_cluster_ws_batch_equals_single(variant):
     """Uneven streams (some with 0 spectra) of one P = 4096 plan in one batched
-    launch of the warp-specialised cluster kernel: identical to per-stream runs."""
+    launch of a warp-specialised cluster kernel: identical to per-stream runs."""
     import torch
     P, T = 4096, 16
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN)
-    assert plan.variant == 1
+    plan.variant = variant
     lens = [P * 20 + 3, P * 3, P * 15, P * 97 + 11, P * 16, P * 300, P * 41]
     xs = [to_device(synth.small_stream(P, T, n, seed=70 + i).generate()) for i, n in enumerate(lens)]
     singles = [plan.execute(x).clone() if plan.out_spectra(x.numel()) > 0 else None for x in xs]
@@ -339,18 +345,39 @@ def test_cluster_ws_batch_equals_single():
             assert torch.all(o == 9.0)
 
 
-@pytest.mark.parametrize("variant", [5])
-def test_ws_repeatable_at_scale(variant):
-    """The warp-specialised P = 1024 kernel over 4096 spectra, run six times:
-    bitwise identical (a race on the TMA ring would corrupt runs of spectra)."""
+@pytest.mark.parametrize("P,variant", [(1024, 5), (4096, 1), (4096, 2), (2048, 2)])
+def test_ws_repeatable_at_scale(P, variant):
+    """A warp-specialised kernel over 4096 spectra (P = 1024: one stream; P =
+    2048, 4096: 16 streams of 256 spectra in one launch, every cluster with
+    several segments), run six times: bitwise identical (a race on the TMA
+    ring or a receive slot would corrupt runs of spectra); sampled rows
+    against the oracle."""
     import torch
-    P, T = 1024, 16
-    xd = to_device(synth.small_stream(P, T, P * (4096 + T - 1), seed=17).generate())
+    T = 16
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HAMMING)
     plan.variant = variant
-    a = plan.execute(xd).clone()
+    if P == 1024:
+        xs = [synth.small_stream(P, T, P * (4096 + T - 1), seed=17).generate()]
+    else:
+        xs = [synth.small_stream(P, T, P * (256 + T - 1) + 9, seed=17 + i).generate() for i in range(16)]
+    xd = [to_device(x) for x in xs]
+    outs = [torch.empty((plan.out_spectra(x.size), P), dtype=torch.complex64, device="cuda") for x in xs]
+
+    def run():
+        pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xd, outs)])
+        torch.cuda.synchronize()
+        return [o.clone() for o in outs]
+
+    a = run()
     for _ in range(5):
-        assert torch.equal(plan.execute(xd), a)
+        b = run()
+        assert all(torch.equal(u, v) for u, v in zip(a, b))
+    assert plan.status() == pkg.PFB_OK
+    for i in (0, len(xs) - 1):
+        S = a[i].shape[0]
+        rows = [0, S // 2, S - 1]
+        ref = np.concatenate([reference(xs[i], synth.IN_C64, P, T, synth.WIN_HAMMING, s0=r, ns=1) for r in rows])
+        assert_close(a[i][rows].cpu().numpy(), ref, what=f"P={P} variant {variant} stream {i}")
 
 
 HOP = [(1024, 16, synth.IN_C64, 512, 0), (1024, 16, synth.IN_C64, 256, 1), (256, 8, synth.IN_R32, 64, 0),

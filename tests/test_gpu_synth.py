@@ -88,9 +88,9 @@ def test_synthesis_is_the_adjoint_of_the_analysis_kernel(P, T):
 
 def test_synthesis_rejects_unsupported_plans():
     import torch
-    X = to_device(_spectra(4, 256, 1))
+    X = to_device(_spectra(4, 64, 1))
     with pytest.raises(pkg.PFBError) as e:
-        pkg.Plan(256, 8).synthesize(X)
+        pkg.Plan(64, 8, path=pkg.PFB_DFT_GEMM_BF16X3).synthesize(X)   # no split-bf16 kernel below P = 128
     assert e.value.status == pkg.PFB_ERR_UNSUPPORTED
     X = to_device(_spectra(4, 1024, 1))
     with pytest.raises(pkg.PFBError) as e:
@@ -102,3 +102,54 @@ def test_synthesis_rejects_unsupported_plans():
         plan.synthesize(X, out=small)
     assert e.value.status == pkg.PFB_ERR_INVALID
     assert plan.synth_out_samples(0) == 0
+
+
+# the routes other than the fused kernel: the FP32 inverse FFT or the split-bf16
+# product with the conjugate DFT matrix, then the adjoint per-branch FIR
+GENERIC = [(4096, 16, pkg.PFB_DFT_FFT_F32, 29, 0), (2048, 8, pkg.PFB_DFT_FFT_F32, 13, 1),
+           (16, 4, pkg.PFB_DFT_FFT_F32, 40, 0), (4, 1, pkg.PFB_DFT_FFT_F32, 9, 0),
+           (256, 40, pkg.PFB_DFT_FFT_F32, 50, 1), (1024, 64, pkg.PFB_DFT_FFT_F32, 3, 0),
+           (256, 8, pkg.PFB_DFT_FFT_F32, 33, 0), (64, 3, pkg.PFB_DFT_GEMM_F32, 17, 0),
+           (1024, 16, pkg.PFB_DFT_GEMM_F32, 5, 1), (1024, 16, pkg.PFB_DFT_GEMM_BF16X3, 37, 0),
+           (4096, 16, pkg.PFB_DFT_GEMM_BF16X3, 21, 1), (256, 5, pkg.PFB_DFT_GEMM_BF16X3, 130, 0),
+           (128, 16, pkg.PFB_DFT_GEMM_BF16X3, 7, 0), (2048, 30, pkg.PFB_DFT_GEMM_BF16X3, 4, 0)]
+
+
+@pytest.mark.parametrize("P,T,path,S,rev", GENERIC)
+def test_synthesis_routes_match_oracle(P, T, path, S, rev):
+    """Every P, T up to 64 and every DFT path at hop P: the FP32 routes at the
+    FP32 bound, the split-bf16 route (tensor-core product with the conjugate
+    DFT matrix) at the split-bf16 bound, and bitwise repeatable."""
+    import torch
+    from gpu_common import TOL_BF16X3, TOL_MAX_BF16X3
+    X = _spectra(S, P, P + T + S)
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, path,
+                    tap_order=pkg.PFB_TAPS_CONVOLUTION if rev else pkg.PFB_TAPS_CORRELATION)
+    Xd = to_device(X)
+    xh = plan.synthesize(Xd)
+    again = plan.synthesize(Xd)
+    torch.cuda.synchronize()
+    assert torch.equal(xh, again)
+    assert plan.status() == pkg.PFB_OK
+    ref = oracle.synth(X.astype(np.complex128), P, T, _taps(P, T, synth.WIN_HANN, rev))
+    tol = (TOL_BF16X3, TOL_MAX_BF16X3) if path == pkg.PFB_DFT_GEMM_BF16X3 else (TOL_F32, TOL_MAX_F32)
+    e2, _ = assert_close(xh.cpu().numpy(), ref, *tol, what=f"synthesis P={P} T={T} path={path} rev={rev}")
+    if path == pkg.PFB_DFT_GEMM_BF16X3:
+        assert e2 > 1e-8  # the split arithmetic really ran
+
+
+@pytest.mark.parametrize("P,T,path", [(4096, 16, pkg.PFB_DFT_FFT_F32), (2048, 12, pkg.PFB_DFT_FFT_F32),
+                                      (1024, 16, pkg.PFB_DFT_GEMM_BF16X3)])
+def test_synthesis_routes_are_the_adjoint_of_the_analysis(P, T, path):
+    """<A x, Y> = P <x, synth(Y)> with the analysis kernel of the same plan."""
+    S = 40
+    rng = np.random.default_rng(P + T + path)
+    x = (rng.standard_normal((S + T - 1) * P) + 1j * rng.standard_normal((S + T - 1) * P)).astype(np.complex64)
+    Y = _spectra(S, P, 9)
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_BLACKMAN, path)
+    Ax = plan.execute(to_device(x)).cpu().numpy().astype(np.complex128)
+    Sy = plan.synthesize(to_device(Y)).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(Ax, Y.astype(np.complex128))
+    rhs = P * np.vdot(x.astype(np.complex128), Sy)
+    tol = 1e-4 if path == pkg.PFB_DFT_GEMM_BF16X3 else 1e-5
+    assert abs(lhs - rhs) <= tol * np.linalg.norm(Ax) * np.linalg.norm(Y)
