@@ -297,7 +297,7 @@ WS_CLUSTER = [(4096, 16, synth.IN_C64, 43), (2048, 16, synth.IN_CI8, 43), (4096,
 @pytest.mark.parametrize("P,T,dt,S", WS_CLUSTER)
 def test_cluster_variants_match_oracle(P, T, dt, S):
     """P = 2048 / 4096 on a CTA cluster: variant 0 (synchronous), variant 1
-    (warp-specialised, cross-CTA step in the FFT warps) and variant 2
+    (warp-specialised, cross-CTA step in the FFT warps), variant 2
     (warp-specialised, one exchange from the FIR warps' radix-4 step to the
     receiving FFT warps' radix-CS step) against the oracle; every
     warp-specialised variant is bitwise reproducible."""

@@ -261,3 +261,39 @@ def test_state_import_rejects_foreign_blobs():
     srv.close_stream(s1)
     srv.close_stream(s2)
     srv.close()
+
+
+def test_submit_chunks_equals_single_submits_and_ticket_times():
+    """pfb_submit_chunks (n chunks of one buffer in one call) gives the same
+    spectra as chunk-by-chunk submission, bit for bit; pfb_ticket_times
+    reports the server's submit and completion times on the steady clock."""
+    import torch
+    P, T, chunk, nch = 4096, 16, 1 << 16, 8
+    x = to_device(synth.small_stream(P, T, chunk * nch, in_dtype=synth.IN_CI8, seed=77).generate())
+    plan = pkg.Plan(P, T, pkg.PFB_IN_CI8, pkg.PFB_WIN_BLACKMAN)
+    srv = pkg.Server(hbm_budget_bytes=1 << 30, max_slots=8)
+    want = _chunked(srv, plan, x, chunk)
+    sid = srv.open_stream(plan)
+    out = torch.full((want.shape[0], P), 5.0, dtype=torch.complex64, device="cuda")
+    t_before = time.monotonic()
+    tks = srv.submit_chunks(sid, x, nch, chunk, out)
+    assert len(tks) == nch and len(set(tks)) == nch
+    for t in tks:
+        assert srv.wait(t, 20000) == pkg.PFB_OK
+    t_after = time.monotonic()
+    torch.cuda.synchronize()
+    assert torch.equal(out, want)
+    prev_done = 0.0
+    for t in tks:
+        ts, td = srv.ticket_times(t)
+        assert t_before - 1e-3 <= ts <= td <= t_after + 1e-3
+        assert td >= prev_done   # chunks of one stream complete in order
+        prev_done = td
+    # a too-small output is rejected before anything is submitted past it
+    sid2 = srv.open_stream(plan)
+    small = torch.empty((3, P), dtype=torch.complex64, device="cuda")
+    with pytest.raises(pkg.PFBError) as e:
+        srv.submit_chunks(sid2, x, nch, chunk, small)
+    assert e.value.status == pkg.PFB_ERR_INVALID
+    srv.close_stream(sid)
+    assert srv.close() in (pkg.PFB_OK,)
