@@ -605,6 +605,7 @@ def run_serving(pkg, n_requests, rate_hz, warm_s, device, budget_bytes, seed_off
     cv = threading.Condition()
     done_flag = [False]
     lat, failed = [], [0]
+    open_waits = [0]
     t_first_done = [None]
 
     def collector():
@@ -636,7 +637,17 @@ def run_serving(pkg, n_requests, rate_hz, warm_s, device, budget_bytes, seed_off
             if dt > 2e-4:
                 time.sleep(dt - 1e-4)
         b = i % nbuf
-        sid = srv.open_stream(plan)
+        while True:
+            try:
+                sid = srv.open_stream(plan)
+                break
+            except pkg.PFBError as e:
+                # admission: the budget holds no room for another stream's resident state
+                # yet; the request waits (its latency still counts from its arrival)
+                if e.status not in (pkg.PFB_ERR_OOM, pkg.PFB_ERR_BUSY) or time.monotonic() - t_arr > 5.0:
+                    raise
+                open_waits[0] += 1
+                time.sleep(2e-5)
         tks = srv.submit_chunks(sid, bufs[b], nch, wl.chunk_samples, outs[b])
         with cv:
             pending.append((i, sid, tks[-1], t_arr))
@@ -666,21 +677,30 @@ def run_serving(pkg, n_requests, rate_hz, warm_s, device, budget_bytes, seed_off
             "chunk_p50_us": stats["p50_latency_us"], "chunk_p99_us": stats["p99_latency_us"],
             "mean_batch": stats["batched_requests"] / max(stats["batches"], 1),
             "failed": stats["failed"] + failed[0], "peak_reserved_bytes": stats["peak_reserved_bytes"],
-            "budget_bytes": budget_bytes,
+            "budget_bytes": budget_bytes, "stream_open_waits": open_waits[0],
             "latency": "scheduled arrival -> the server's completion time of the request's last chunk"}
 
 
 def serving_block(pkg, device, n_requests):
     out = {"p99_bound_us": 1000.0}
-    out["budget_40GB"] = run_serving(pkg, n_requests, 2000.0, 1.0, device, 40 << 30)
-    out["budget_64MB"] = run_serving(pkg, max(2000, n_requests // 4), 2000.0, 1.0, device, 64 << 20, seed_offset=1)
-    # a budget below two requests' chunks (about 10 MB each): admission binds
-    out["budget_16MB"] = run_serving(pkg, max(2000, n_requests // 4), 2000.0, 1.0, device, 16 << 20, seed_offset=2)
+
+    def guarded(*a, **k):
+        try:
+            return run_serving(*a, **k)
+        except Exception as e:  # reported, not hidden
+            return {"error": repr(e)}
+
+    out["budget_40GB"] = guarded(pkg, n_requests, 2000.0, 1.0, device, 40 << 30)
+    out["budget_64MB"] = guarded(pkg, max(2000, n_requests // 4), 2000.0, 1.0, device, 64 << 20, seed_offset=1)
+    # a budget below two requests' chunks (about 10 MB each) and their resident state: admission
+    # binds, chunks queue and new streams wait for room (stream_open_waits)
+    out["budget_16MB"] = guarded(pkg, max(2000, n_requests // 4), 2000.0, 1.0, device, 16 << 20, seed_offset=2)
     sweep = []
     best = None
     for rate in (2000.0, 4000.0, 8000.0, 12000.0, 16000.0, 32000.0):
-        r = run_serving(pkg, max(2000, int(rate)), rate, 0.25, device, 40 << 30, seed_offset=int(rate))
-        if r is None:
+        r = guarded(pkg, max(2000, int(rate)), rate, 0.25, device, 40 << 30, seed_offset=int(rate))
+        if r is None or "error" in r:
+            sweep.append(r)
             break
         sweep.append({k: r[k] for k in ("offered_req_per_s", "achieved_req_per_s", "p50_us", "p99_us", "gsps",
                                          "mean_batch", "failed")})
