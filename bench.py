@@ -263,6 +263,18 @@ def workload_c2():
     return spec, spec.generate()
 
 
+def c3_config(path, P, T, nstreams, n, spectra):
+    """The headline workload's config; both arms print exactly this dict."""
+    return {"workload": C3_WORKLOAD + "; one pfb_execute_batch over all streams per step, "
+                        + {"fft": "FIR + FFT path (FP32)", "bf16x3": "FIR + factored split-bf16 tensor-core DFT",
+                           "bf16x3_dense": "FIR + dense split-bf16 DFT-matrix GEMM"}[path],
+            "P": P, "T": T, "streams": nstreams, "n_samples": n, "spectra": spectra,
+            "path": {"fft": "fft_f32", "bf16x3": "gemm_bf16x3", "bf16x3_dense": "gemm_bf16x3_dense"}[path],
+            "l2": f"inputs larger than L2: each step reads {n * 8 >> 20} MiB and writes "
+                  f"{spectra * P * 8 >> 20} MiB (> 129 MB L2); no flush between steps",
+            "replicas": "each rank channelises its own copy of the workload (weak scaling, no collective)"}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the headline workload, timed on the
     host cores (rank 0 only); each step = 16 spectra of one c3 stream."""
@@ -291,11 +303,10 @@ def run_reference(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": C3_WORKLOAD + f"; each step = {ns} spectra of one stream (stream = step mod 64) "
-                                            "through the FP64 oracle",
-                   "P": P, "T": T, "streams": len(xs), "n_samples_per_stream": int(xs[0].size)},
+        "config": c3_config(args.path, P, T, len(xs), sum(int(x.size) for x in xs), len(xs) * S),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle",
-                         "sample": f"{ns} spectra ({ns * P} input samples at hop P) per step"},
+                         "sample": f"{ns} spectra ({ns * P} input samples at hop P) of one stream per step "
+                                   "(stream = step mod 64), through the FP64 oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -859,15 +870,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": C3_WORKLOAD + "; one pfb_execute_batch over all streams per step, "
-                               + {"fft": "FIR + FFT path (FP32)", "bf16x3": "FIR + factored split-bf16 tensor-core DFT",
-                                  "bf16x3_dense": "FIR + dense split-bf16 DFT-matrix GEMM"}[args.path],
-                   "P": P, "T": T, "streams": len(xs_host), "n_samples": n, "spectra": len(xs_host) * S,
-                   "path": {"fft": "fft_f32", "bf16x3": "gemm_bf16x3", "bf16x3_dense": "gemm_bf16x3_dense"}[args.path],
-                   "variant": plan.variant,
-                   "l2": f"inputs larger than L2: each step reads {n * 8 >> 20} MiB and writes "
-                         f"{len(xs_host) * S * P * 8 >> 20} MiB (> 129 MB L2); no flush between steps",
-                   "replicas": "each rank channelises its own copy of the workload (weak scaling, no collective)"},
+        "config": c3_config(args.path, P, T, len(xs_host), n, len(xs_host) * S),
         "roofline": roofline,
         "gpu_launches": gpu_launches,
         "clocks": clocks,

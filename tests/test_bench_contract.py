@@ -30,6 +30,10 @@ def test_reference_arm_line():
     assert d["steps"] == 3 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["config"]["workload"].startswith("c3")
+    # the GPU arm prints this same dict for its default run (64 streams, FFT path)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.c3_config("fft", 4096, 16, 64, 64 << 20, 64 * 241)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
