@@ -7,12 +7,15 @@
 // equal to their compiled tap count 4, 8 or 16.
 #include "fft_cluster.cuh"
 #include "fft_wc2.cuh"
+#include "fft_wcf.cuh"
 #include "fft_ws_cluster.cuh"
 
 namespace pfb {
 
 int64_t cluster_units(int64_t S) { return (S + 7) / 8; }
 int64_t fft_cluster_units(const Plan &plan, int64_t S) { return plan.variant >= 1 ? S : cluster_units(S); }
+
+bool wcf_supported(const Plan &plan) { return plan.P == 4096 && plan.T == plan.TT && (plan.TT == 4 || plan.TT == 8 || plan.TT == 16); }
 
 bool ws_cluster_supported(const Plan &plan) {
     return (plan.P == 2048 || plan.P == 4096) && plan.T == plan.TT && (plan.TT == 4 || plan.TT == 8 || plan.TT == 16);
@@ -100,6 +103,66 @@ static pfb_status launch_wc2_k(LaunchArgs &a, cudaStream_t stream) {
     g_launches++;
     if (e != cudaSuccess) return cuda_fail(e, "launch k_fft_wc2");
     return PFB_OK;
+}
+
+template <int TT, int IN>
+static pfb_status launch_wcf_k(LaunchArgs &a, cudaStream_t stream) {
+    using C = WcfCfg<TT, IN>;
+    auto k = k_fft_wcf<TT, IN>;
+    static int cap_clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C::CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cap_clusters == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fft_wcf)");
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cfg.gridDim = dim3((unsigned)(sms / C::CS * C::CS), 1, 1);
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess || n < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                                                        "cudaOccupancyMaxActiveClusters(k_fft_wcf)");
+        cap_clusters = n;
+    }
+    int64_t clusters = a.nunits < cap_clusters ? a.nunits : cap_clusters;
+    if (clusters < 1) return PFB_OK;
+    if ((a.nunits + clusters - 1) / clusters > INT32_MAX - 64)  // 32-bit segment counters in the kernel
+        return fail(PFB_ERR_INVALID, "too many spectra for one cluster launch");
+    a.units_per_cta = (int32_t)((a.nunits + clusters - 1) / clusters);
+    clusters = (a.nunits + a.units_per_cta - 1) / a.units_per_cta;
+    cfg.gridDim = dim3((unsigned)(clusters * C::CS), 1, 1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
+    g_launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_fft_wcf");
+    return PFB_OK;
+}
+
+static pfb_status launch_wcf(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    if (plan.P != 4096) return fail(PFB_ERR_UNSUPPORTED, "cluster variant 3: P must be 4096");
+    for (int i = 0; i < a.nstreams; ++i)
+        if (a.s[i].T != plan.TT) return fail(PFB_ERR_UNSUPPORTED, "cluster variant 3 needs T in {4, 8, 16}");
+    switch (plan.in_dtype * 100 + plan.TT) {
+    case PFB_IN_C64 * 100 + 4: return launch_wcf_k<4, PFB_IN_C64>(a, stream);
+    case PFB_IN_C64 * 100 + 8: return launch_wcf_k<8, PFB_IN_C64>(a, stream);
+    case PFB_IN_C64 * 100 + 16: return launch_wcf_k<16, PFB_IN_C64>(a, stream);
+    case PFB_IN_R32 * 100 + 4: return launch_wcf_k<4, PFB_IN_R32>(a, stream);
+    case PFB_IN_R32 * 100 + 8: return launch_wcf_k<8, PFB_IN_R32>(a, stream);
+    case PFB_IN_R32 * 100 + 16: return launch_wcf_k<16, PFB_IN_R32>(a, stream);
+    case PFB_IN_CI8 * 100 + 4: return launch_wcf_k<4, PFB_IN_CI8>(a, stream);
+    case PFB_IN_CI8 * 100 + 8: return launch_wcf_k<8, PFB_IN_CI8>(a, stream);
+    case PFB_IN_CI8 * 100 + 16: return launch_wcf_k<16, PFB_IN_CI8>(a, stream);
+    default: return fail(PFB_ERR_UNSUPPORTED, "cluster variant 3: no kernel for this T/dtype");
+    }
 }
 
 template <int CS>
@@ -200,6 +263,7 @@ bool fft_cluster_supported(int P, int T) { return (P == 2048 || P == 4096) && T 
 
 pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     a.aux = plan.d_tw_r2;
+    if (plan.variant == 3) return launch_wcf(plan, a, stream);
     if (plan.variant == 2) {
         switch (plan.P) {
         case 2048: return launch_wc2_cs<2>(plan, a, stream);

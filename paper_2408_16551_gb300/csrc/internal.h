@@ -172,6 +172,7 @@ pfb_status build_tcf_table(Plan &plan);
 pfb_status launch_fft_cluster(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 bool fft_cluster_supported(int P, int T);
 bool ws_cluster_supported(const Plan &plan);   // variant 1 of the cluster family
+bool wcf_supported(const Plan &plan);          // variant 3 of the cluster family (P = 4096)
 pfb_status prepare_family(const Plan &plan);
 pfb_status ensure_variant_tables(Plan &plan);
 const float *family_taps(const Plan &plan);   // tap layout the family's kernels read

@@ -70,6 +70,20 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared through L2 only (LSU path; both
+// addresses 16-byte aligned), for gathers of many short runs where one
+// bulk copy per run would be bound by the TMA engine's request rate
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// arrive on mbarrier `bar` once every cp.async this thread issued so far has
+// landed; the arrival is not pre-counted (.noinc), so the barrier's count
+// includes one arrival per issuing thread
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 // L2 prefetch of `bytes` (multiple of 16, 16-byte aligned address) of global memory
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");

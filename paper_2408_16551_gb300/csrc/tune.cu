@@ -79,11 +79,11 @@ static void save_file_cache() {
 // product, 1 = factored (four-step) tensor-core DFT; cluster FFT family:
 // 0 = synchronous, 1 = warp-specialised with the cross-CTA step in the FFT
 // warps, 2 = warp-specialised with one exchange from the FIR warps' radix-4
-// step to the receiving FFT warps
+// step to the receiving FFT warps, 3 = four-step 64 x 64 (P = 4096)
 int family_variants(const Plan &plan) {
     if (plan.family == FAM_FFT_FAST) return 6;
     if (plan.family == FAM_GEMM_BF16X3) return 2;
-    if (plan.family == FAM_FFT_CLUSTER) return 3;
+    if (plan.family == FAM_FFT_CLUSTER) return 4;
     return 1;
 }
 
@@ -92,6 +92,7 @@ int family_variants(const Plan &plan) {
 static bool variant_supported(const Plan &plan, int v) {
     if (plan.family == FAM_FFT_FAST && v == 5) return plan.P >= 128 && plan.T == plan.TT;
     if (plan.family == FAM_GEMM_BF16X3 && v == 1) return tcf_supported(plan);
+    if (plan.family == FAM_FFT_CLUSTER && v == 3) return wcf_supported(plan);
     if (plan.family == FAM_FFT_CLUSTER && v >= 1) return v < 3 && ws_cluster_supported(plan);
     return v >= 0 && v < family_variants(plan);
 }
@@ -99,7 +100,7 @@ static bool variant_supported(const Plan &plan, int v) {
 int default_variant(const Plan &plan) {
     if (family_variants(plan) <= 1) return 0;
     if (plan.family == FAM_GEMM_BF16X3) return tcf_supported(plan) ? 1 : 0;
-    if (plan.family == FAM_FFT_CLUSTER) return ws_cluster_supported(plan) ? 2 : 0;
+    if (plan.family == FAM_FFT_CLUSTER) return wcf_supported(plan) ? 3 : ws_cluster_supported(plan) ? 2 : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_file_cache();
     auto it = g_tune_cache.find(key_of(plan));

@@ -299,31 +299,36 @@ def test_cluster_variants_match_oracle(P, T, dt, S):
     """P = 2048 / 4096 on a CTA cluster: variant 0 (synchronous), variant 1
     (warp-specialised, cross-CTA step in the FFT warps), variant 2
     (warp-specialised, one exchange from the FIR warps' radix-4 step to the
-    receiving FFT warps' radix-CS step) against the oracle; every
-    warp-specialised variant is bitwise reproducible."""
+    receiving FFT warps' radix-CS step) and, for P = 4096, variant 3 (four-step
+    64 x 64: contiguous input and output runs per CTA) against the oracle;
+    every warp-specialised variant is bitwise reproducible."""
     import torch
     n = P * (S + T - 1) + 5
     x = synth.small_stream(P, T, n, in_dtype=dt, seed=P + S).generate()
     ref = reference(x, dt, P, T, synth.WIN_BLACKMAN)
     plan = pkg.Plan(P, T, dt, pkg.PFB_WIN_BLACKMAN)
-    assert plan.num_variants == 3 and plan.variant == 2
+    assert plan.num_variants == 4 and plan.variant == (3 if P == 4096 else 2)
     xd = to_device(x)
     outs = {}
-    for v in (0, 1, 2):
+    ws = (1, 2, 3) if P == 4096 else (1, 2)
+    if P != 4096:
+        with pytest.raises(pkg.PFBError):
+            plan.variant = 3
+    for v in (0,) + ws:
         plan.variant = v
         X = plan.execute(xd)
         torch.cuda.synchronize()
         outs[v] = X.cpu().numpy()
         assert plan.status() == pkg.PFB_OK
         assert_close(outs[v], ref, what=f"cluster variant {v} P={P} T={T} dt={dt} S={S}")
-    for v in (1, 2):
+    for v in ws:
         plan.variant = v
         for _ in range(3):  # a ring or receive slot reused too early shows up as wrong spectra
             again = plan.execute(xd).cpu().numpy()
             assert np.array_equal(again, outs[v]), v
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_cluster_ws_batch_equals_single(variant):
     """Uneven streams (some with 0 spectra) of one P = 4096 plan in one batched
     launch of a warp-specialised cluster kernel: identical to per-stream runs."""
@@ -345,7 +350,7 @@ def test_cluster_ws_batch_equals_single(variant):
             assert torch.all(o == 9.0)
 
 
-@pytest.mark.parametrize("P,variant", [(1024, 5), (4096, 1), (4096, 2), (2048, 2)])
+@pytest.mark.parametrize("P,variant", [(1024, 5), (4096, 1), (4096, 2), (2048, 2), (4096, 3)])
 def test_ws_repeatable_at_scale(P, variant):
     """A warp-specialised kernel over 4096 spectra (P = 1024: one stream; P =
     2048, 4096: 16 streams of 256 spectra in one launch, every cluster with
