@@ -13,7 +13,9 @@
 // bins as 64 runs of 16 consecutive bins per spectrum; one exchange between
 // the CTAs carries B_p2[k1] from the column owner to the row owner.
 //   FIR warps, thread t = 16 t1 + u: the four branches p1 = 16 j + t1 (j < 4)
-//       of column p2; on completion the first radix-4 step of the 64-point
+//       of column p2, the T - 1 pending spectra in registers (a spectrum takes
+//       its last tap and is consumed in the slot the next one starts in); on
+//       completion the first radix-4 step of the 64-point
 //       DFT over p1 (decimation in frequency):
 //       Z_a[t1] = w_64^(t1 a) sum_j y[64 (16 j + t1) + p2] w_4^(j a),  a < 4;
 //   FFT warps, pass A: B_p2[a + 4 b] = sum_{t1} Z_a[t1] w_16^(t1 b); each
@@ -81,7 +83,7 @@ struct WcfCfg {
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16;
     static constexpr int REG_FIR = 208, REG_FFT = 72, REG_PROD = 24;
     static_assert(NFT * REG_FIR + NFFTT * REG_FFT + 128 * REG_PROD <= 65536, "register split");
-    static_assert(TT % SB == 0, "batch rows follow the frame loop's unrolling");
+    static_assert(TT >= 2, "pending-spectrum slots");
     static_assert(DR >= SB && LAG * SB >= DR, "a combine needs its batch sent; pass B needs its combines");
     static_assert(NR > (LAG + 1) * SB + DR / SB, "receive slots for the spectra between a send and its hand-back");
     static_assert(NCP * 16 * 128 == FB, "whole 16-byte pieces per producer thread");
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
         const uint32_t wns = (uint32_t)a.wait_ns;  // at most 4 s (checked on the host)
         const int pcol = 64 * (t >> 4) + 16 * crank + (t & 15);  // branch 1024 j + pcol
         float h[TT][4];
-        float2 pend[TT][4];
+        constexpr int NS = TT - 1;  // register slots of pending spectra
+        float2 pend[NS][4];
         int cur = -1;
         uint32_t pc = 0;  // frames consumed
         uint32_t bc = 0;  // batches handed to pass A
@@ -201,9 +204,12 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
             // cluster's range (units_per_cta, checked on the host)
             const int nspec = (int)(sB - sA);
             const int nfr = nspec + TT - 1;
-            for (int i0 = 0; i0 < nfr && ok; i0 += TT) {
+            // NS = TT - 1 register slots: spectrum s lives in slot s mod NS; at
+            // frame i the slot of spectrum i - NS takes its last tap and is
+            // consumed before spectrum i starts in it
+            for (int i0 = 0; i0 < nfr && ok; i0 += NS) {
 #pragma unroll
-                for (int k = 0; k < TT; ++k) {
+                for (int k = 0; k < NS; ++k) {
                     const int i = i0 + k;
                     if (i < nfr) {
                         const uint32_t slot = pc % NSLOT;
@@ -232,30 +238,29 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                             if (lane == 0 && pc > 0) mbar_arrive(empty0 + 8 * ((pc - 1) % NSLOT));
                         }
                         ++pc;
-                        // frame i contributes h[m] * x to spectrum i - m (register slot (i - m) mod TT)
+                        // frame i contributes h[m] * x to spectrum i - m, slot (i - m) mod NS
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
-#pragma unroll
-                        for (int m = 1; m < TT; ++m) {
-                            const int js = ((k - m) % TT + TT) % TT;
+                        for (int m = 1; m < NS; ++m) {
+                            const int js = ((k - m) % NS + NS) % NS;
 #pragma unroll
                             for (int j = 0; j < 4; ++j) pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
                         }
-                        const int jspec = i - (TT - 1);
+                        const int jspec = i - NS;
                         if (jspec >= 0) {
-                            // ---- spectrum jspec is complete: radix-4 over j into Y ----
-                            const int jslot = (k + 1) % TT;
-                            const int brow = (k + 1) % SB;  // segments start at spectrum 0 and SB divides TT
+                            // ---- spectrum jspec completes in slot k: radix-4 over j into Y ----
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) pend[k][j] = fma2(make_float2(h[NS][j], h[NS][j]), v[j], pend[k][j]);
+                            const int brow = jspec % SB;
                             if (brow == 0 && bc >= 2 &&
                                 !__all_sync(0xffffffffu, mbar_wait32(yempty0 + 8 * (bc & 1), ((bc >> 1) + 1) & 1, wns))) {
                                 ok = false;
                                 break;
                             }
                             float2 *ys = Y + (bc & 1) * C::YBUF + brow * 1024 + t;
-                            const float2 a0 = cadd2(pend[jslot][0], pend[jslot][2]);
-                            const float2 a1 = csub2(pend[jslot][0], pend[jslot][2]);
-                            const float2 a2 = cadd2(pend[jslot][1], pend[jslot][3]);
-                            const float2 a3 = csub2(pend[jslot][1], pend[jslot][3]);
+                            const float2 a0 = cadd2(pend[k][0], pend[k][2]);
+                            const float2 a1 = csub2(pend[k][0], pend[k][2]);
+                            const float2 a2 = cadd2(pend[k][1], pend[k][3]);
+                            const float2 a3 = csub2(pend[k][1], pend[k][3]);
                             const float2 mi_a3 = make_float2(a3.y, -a3.x);  // -i a3
                             const int t1 = t >> 4;
                             ys[0] = cadd2(a0, a2);
@@ -267,11 +272,14 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                                 if (lane == 0) mbar_arrive(yfull0 + 8 * (bc & 1));
                                 ++bc;
                             }
-                            // ---- combine of the spectrum sent DR spectra earlier ----
-                            if (g0 + (uint32_t)jspec >= rc + C::DR && !combine()) {
-                                ok = false;
-                                break;
-                            }
+                        }
+                        // spectrum i starts in slot k
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
+                        // ---- combine of the spectrum sent DR spectra earlier ----
+                        if (jspec >= 0 && g0 + (uint32_t)jspec >= rc + C::DR && !combine()) {
+                            ok = false;
+                            break;
                         }
                     }
                 }
@@ -288,16 +296,18 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
         const int hf = 2 * (w & 1) + (lane >> 4);   // pass A: a; pass B: k2a
         const int l16 = lane & 15;                  // pass A: u; pass B: kl
         WcfMeta *mym = meta + w * 4;
+        const uint32_t wns = (uint32_t)a.wait_ns;  // at most 4 s (checked on the host)
         uint32_t nA = 0, nB = 0, gA = 0;
         bool ok = true, more = true;
         int si = 0;
-        int64_t sA = 0, sB = 0, s0 = 0, nspec = 0;
+        int64_t sA = 0, sB = 0;
+        int s0 = 0, nspec = 0;  // segment-relative (a segment is at most one cluster's range)
         const uint32_t r_loc = smem_u32(R);
         while (ok) {
             while (more && s0 >= nspec) {
                 if (ws_next_segment(a, range, si, sA, sB)) {
                     s0 = 0;
-                    nspec = sB - sA;
+                    nspec = (int)(sB - sA);
                 } else {
                     more = false;
                 }
@@ -305,7 +315,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
             if (more) {
                 // ---- pass A of batch nA: 16-point DFTs over t1, sent to the row owners ----
                 const StreamDesc &d = a.s[si];
-                const int nrows = (int)min((int64_t)SB, nspec - s0);
+                const int nrows = min(SB, nspec - s0);
                 if (lane == 0) {
                     WcfMeta m;
                     m.out = d.out + (sA + s0) * d.ldo;
@@ -315,7 +325,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                     m.pad_ = 0;
                     mym[nA & 3] = m;
                 }
-                if (!__all_sync(0xffffffffu, mbar_wait(yfull0 + 8 * (nA & 1), (nA >> 1) & 1, a.wait_ns))) {
+                if (!__all_sync(0xffffffffu, mbar_wait32(yfull0 + 8 * (nA & 1), (nA >> 1) & 1, wns))) {
                     ok = false;
                     break;
                 }
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                     const uint32_t g = gA + (uint32_t)row, rs = g % NR;
                     // every receiver handed this slot's previous use back
                     if (g >= NR &&
-                        !__all_sync(0xffffffffu, mbar_wait(rempty0 + 8u * rs, ((g / NR) + 1) & 1, a.wait_ns))) {
+                        !__all_sync(0xffffffffu, mbar_wait32(rempty0 + 8u * rs, ((g / NR) + 1) & 1, wns))) {
                         ok = false;
                         break;
                     }
@@ -354,7 +364,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                 const WcfMeta m = mym[nB & 3];
                 if (row < m.nrows) {
                     const uint32_t g = m.g + (uint32_t)row, rs = g % NR;
-                    if (!__all_sync(0xffffffffu, mbar_wait(r2full0 + 8u * rs, (g / NR) & 1, a.wait_ns))) {
+                    if (!__all_sync(0xffffffffu, mbar_wait32(r2full0 + 8u * rs, (g / NR) & 1, wns))) {
                         ok = false;
                         break;
                     }
