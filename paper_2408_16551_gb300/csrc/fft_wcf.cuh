@@ -21,8 +21,9 @@
 //   FFT warps, pass A: B_p2[a + 4 b] = sum_{t1} Z_a[t1] w_16^(t1 b); each
 //       value goes as an 8-byte asynchronous store into the receive slot of
 //       CTA (a + 4 b) / 16, whose mbarrier counts the bytes;
-//   FIR warps of the receiver, thread t = 16 kl + u, DR spectra later: the
-//       radix-4 step over the source CTA c of the 64-point DFT over p2 =
+//   combine in the receiver (even spectra: FIR warps, thread t = 16 kl + u,
+//       DR spectra later; odd spectra: FFT warps, one batch after pass A):
+//       the radix-4 step over the source CTA c of the 64-point DFT over p2 =
 //       16 c + u, with k2 = k2a + 4 k2b:
 //       S_k2a = w_P^(u (k1 + 64 k2a)) sum_c w_4^(c k2a) w_256^(c k1) B_(16c+u)[k1],
 //       in place in the receive slot;
@@ -35,7 +36,7 @@
 // named barrier).  Hand-overs: ring full/empty (producer <-> FIR), Y
 // full/empty per batch of SB spectra (FIR -> pass A), receive slot rfull
 // (bytes from the four senders; armed by the pass-B warps for its next use
-// before they hand it back), r2full (combine done, FIR -> pass B) and rempty
+// before they hand it back), r2full (combine done -> pass B) and rempty
 // in every sender (the pass-B warps of every receiver hand the slot back
 // with relaxed remote arrivals).  Every wait is bounded (the launch's
 // wait_ns); a timeout sets the error word and the roles wind down; all
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
         }
         for (int i = 0; i < NR; ++i) {
             mbar_init(rfull0 + 8 * i, 1);        // the receiver's arm + RB bytes from the four senders
-            mbar_init(r2full0 + 8 * i, C::NFIRW);  // every FIR warp has combined its part
+            mbar_init(r2full0 + 8 * i, C::NFIRW);  // 8 FIR warps, or 4 FFT warps arriving with count 2
             mbar_init(rempty0 + 8 * i, 2 * 4);   // the two pass-B warps of the slot's row in each receiver
         }
         mbar_init_fence();
@@ -188,6 +189,14 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
             if (lane == 0) mbar_arrive(r2full0 + 8u * rs);
             ++rc;
             return true;
+        };
+        // the FIR warps combine the even spectra, the FFT warps the odd ones
+        auto combine_or_skip = [&]() -> bool {
+            if (rc & 1) {
+                ++rc;
+                return true;
+            }
+            return combine();
         };
         int si;
         int64_t sA, sB;
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
 #pragma unroll
                         for (int j = 0; j < 4; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
                         // ---- combine of the spectrum sent DR spectra earlier ----
-                        if (jspec >= 0 && g0 + (uint32_t)jspec >= rc + C::DR && !combine()) {
+                        if (jspec >= 0 && g0 + (uint32_t)jspec >= rc + C::DR && !combine_or_skip()) {
                             ok = false;
                             break;
                         }
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
             }
             g0 += (uint32_t)nspec;
         }
-        while (ok && rc < g0) ok = combine();  // the last DR spectra of the range
+        while (ok && rc < g0) ok = combine_or_skip();  // the last DR spectra of the range
         if (!ok) *abort_flag = 1;
     } else if (warp < C::PRODW) {
         // ======================= FFT warps =======================
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
         const int l16 = lane & 15;                  // pass A: u; pass B: kl
         WcfMeta *mym = meta + w * 4;
         const uint32_t wns = (uint32_t)a.wait_ns;  // at most 4 s (checked on the host)
-        uint32_t nA = 0, nB = 0, gA = 0;
+        uint32_t nA = 0, nB = 0, nC = 0, gA = 0;
         bool ok = true, more = true;
         int si = 0;
         int64_t sA = 0, sB = 0;
@@ -345,11 +354,14 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                     // B_p2[hf + 4 b] -> CTA b / 4, entry [c][kl = hf + 4 (b mod 4)][u]
                     const uint32_t e_loc = r_loc + (uint32_t)(rs * C::RSLOT + crank * RS + RK * hf + l16) * 8u;
                     const uint32_t b_loc = rfull0 + 8u * rs;
+                    // one address translation per destination CTA: a CTA's shared memory
+                    // is one contiguous range of the cluster window
 #pragma unroll
-                    for (int b = 0; b < 16; ++b) {
-                        const uint32_t dst = (uint32_t)(b >> 2);
-                        st_async_v2(mapa_shared(e_loc + (uint32_t)(RK * 4 * (b & 3)) * 8u, dst), v[b],
-                                    mapa_shared(b_loc, dst));
+                    for (int dst = 0; dst < 4; ++dst) {
+                        const uint32_t e_rem = mapa_shared(e_loc, (uint32_t)dst);
+                        const uint32_t b_rem = mapa_shared(b_loc, (uint32_t)dst);
+#pragma unroll
+                        for (int be = 0; be < 4; ++be) st_async_v2(e_rem + (uint32_t)(RK * 4 * be) * 8u, v[4 * dst + be], b_rem);
                     }
                 }
                 __syncwarp();
@@ -358,7 +370,41 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                 gA += (uint32_t)nrows;
                 ++nA;
             }
-            if (nA - nB > (uint32_t)C::LAG || (!more && nB < nA)) {
+            if (nC < nA && (!more || nA - nC > 1)) {
+                // ---- combine of the odd spectra of batch nC (the FIR warps take the even ones) ----
+                __syncwarp();
+                const WcfMeta m = mym[nC & 3];
+#pragma unroll 1
+                for (int row2 = 0; row2 < m.nrows && ok; ++row2) {
+                    const uint32_t g = m.g + (uint32_t)row2, rs = g % NR;
+                    if ((g & 1) == 0) continue;
+                    if (!__all_sync(0xffffffffu, mbar_wait32(rfull0 + 8u * rs, (g / NR) & 1, wns))) {
+                        ok = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int tt = 32 * w + lane + 128 * hh;  // 16 kl + u
+                        float2 *q = R + rs * C::RSLOT + RK * (tt >> 4) + (tt & 15);
+                        const float2 r0 = q[0];
+                        const float2 r1 = cmul(q[RS], twr[tt]);
+                        const float2 r2 = cmul(q[2 * RS], twr[256 + tt]);
+                        const float2 r3 = cmul(q[3 * RS], twr[512 + tt]);
+                        const float2 a0 = cadd2(r0, r2), a1 = csub2(r0, r2);
+                        const float2 a2 = cadd2(r1, r3), a3 = csub2(r1, r3);
+                        const float2 mi_a3 = make_float2(a3.y, -a3.x);  // -i a3
+                        q[0] = cmul(cadd2(a0, a2), twr[768 + tt]);
+                        q[RS] = cmul(cadd2(a1, mi_a3), twr[1024 + tt]);
+                        q[2 * RS] = cmul(csub2(a0, a2), twr[1280 + tt]);
+                        q[3 * RS] = cmul(csub2(a1, mi_a3), twr[1536 + tt]);
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_n(r2full0 + 8u * rs, 2);  // 4 FFT warps x 2 = the 8 FIR arrivals
+                }
+                if (!ok) break;
+                ++nC;
+            }
+            if (nB < nC && (!more || nA - nB > (uint32_t)C::LAG)) {
                 // ---- pass B of batch nB: 16-point DFTs over u, bins to HBM ----
                 __syncwarp();
                 const WcfMeta m = mym[nB & 3];
@@ -382,7 +428,7 @@ __global__ void __launch_bounds__(WcfCfg<TT, IN>::NTHREADS, 1) k_fft_wcf(const _
                     if (lane < 4) mbar_arrive_cluster_relaxed(mapa_shared(rempty0 + 8u * rs, (uint32_t)lane));
                 }
                 ++nB;
-            } else if (!more) {
+            } else if (!more && nB == nA) {
                 break;
             }
         }
