@@ -595,6 +595,7 @@ def run_serving(pkg, n_requests, rate_hz, warm_s, device, budget_bytes, seed_off
     requests in arrival order and closes their streams.  Requests arriving in
     the first warm_s seconds are served but not counted."""
     import collections
+    import gc
     import threading
     import numpy as np
     import torch
@@ -638,6 +639,10 @@ def run_serving(pkg, n_requests, rate_hz, warm_s, device, budget_bytes, seed_off
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
+    # no cyclic garbage collection while requests are timed (a full collection
+    # with the torch objects alive has been seen to pause the submitting thread)
+    gc.collect()
+    gc.disable()
     t0 = time.monotonic() + 0.01
     for i, ta in enumerate(arrivals):
         t_arr = t0 + ta
@@ -668,6 +673,7 @@ def run_serving(pkg, n_requests, rate_hz, warm_s, device, budget_bytes, seed_off
         cv.notify()
     th.join()
     t_end = time.monotonic()
+    gc.enable()
     stats = srv.stats()
     srv.close()
     plan.close()
@@ -700,6 +706,9 @@ def serving_block(pkg, device, n_requests):
             return run_serving(*a, **k)
         except Exception as e:  # reported, not hidden
             return {"error": repr(e)}
+        finally:
+            import gc
+            gc.enable()
 
     out["budget_40GB"] = guarded(pkg, n_requests, 2000.0, 1.0, device, 40 << 30)
     out["budget_64MB"] = guarded(pkg, max(2000, n_requests // 4), 2000.0, 1.0, device, 64 << 20, seed_offset=1)
