@@ -330,19 +330,30 @@ def time_batch(pkg, entries, steps, warmup, stream):
 
 
 def time_path(pkg, plan, xs, outs, steps, warmup, stream):
-    """Per-launch CUDA-event timing of plan.execute over rotating buffers."""
+    """Mean ms per plan.execute over rotating buffers (two events around the
+    timed launches, as for the headline), and the per-launch durations of a
+    separate pass with an event between launches."""
     import torch
     for i in range(warmup):
         plan.execute(xs[i % len(xs)], out=outs[i % len(outs)], stream=stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    ev[0].record(stream)
+    e0.record(stream)
     for i in range(steps):
+        plan.execute(xs[i % len(xs)], out=outs[i % len(outs)], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mean = e0.elapsed_time(e1) / steps
+    n_per = min(steps, 10)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_per + 1)]
+    ev[0].record(stream)
+    for i in range(n_per):
         plan.execute(xs[i % len(xs)], out=outs[i % len(outs)], stream=stream)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
-    return ev[0].elapsed_time(ev[-1]) / steps, per
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(n_per)]
+    return mean, per
 
 
 def c3_paths(pkg, xs_d, xs_host, specs, stream, reps, names):
