@@ -14,7 +14,8 @@ Printed as one JSON line (rank 0).  Besides the headline value it reports:
   paths             GSample/s and sampled rel. L2 error vs the FP64 oracle of
                     the DFT routes on the same workload: FP32 FFT, factored
                     split-bf16 tensor-core DFT, dense split-bf16 DFT-matrix
-                    GEMM, FP32 SIMT DFT-matrix GEMM
+                    GEMM (fused, and in two passes: FIR to a pre-tiled workspace, then
+                    a pipelined tcgen05 GEMM), FP32 SIMT DFT-matrix GEMM
   cpu_baseline      the FP64 oracle on the host cores, on a bounded sample
   cpu_baseline_numpy  a paper-style NumPy FP32 PFB (reshape, per-tap
                     multiply-add, np.fft.fft), one process
@@ -366,6 +367,7 @@ def c3_paths(pkg, xs_d, xs_host, specs, stream, reps, names):
     out = {}
     routes = {"gemm_bf16x3": (pkg.PFB_DFT_GEMM_BF16X3, 1, "bf16x3/f32acc"),
               "gemm_bf16x3_dense": (pkg.PFB_DFT_GEMM_BF16X3, 0, "bf16x3/f32acc"),
+              "gemm_bf16x3_dense_2pass": (pkg.PFB_DFT_GEMM_BF16X3, 2, "bf16x3/f32acc"),
               "gemm_f32": (pkg.PFB_DFT_GEMM_F32, None, "f32")}
     for name in names:
         path, variant, dt = routes[name]
@@ -387,7 +389,9 @@ def c3_paths(pkg, xs_d, xs_host, specs, stream, reps, names):
                 # executed bf16 tensor flop per sample: factored 32 x 32 route 1536
                 # (two products of 32 rows x 64 x 64, three split terms, per 1024
                 # samples, plus the CUDA-core radix-4 cross step); dense DFT-matrix
-                # product 24 P (2P x 2P real block form, three split terms)
+                # product 24 P (2P x 2P real block form, three split terms; the
+                # two-pass variant also multiplies the padding rows of each
+                # stream's last 128-spectrum tile, not counted here)
                 fps = 1536 if plan.variant == 1 else 24 * P
                 tfl = n_total * fps / (ms * 1e-3) / 1e12
                 ent["tensor"] = {"executed_tflops": tfl, "flop_per_sample": fps, "frac_of_sustained_bf16": tfl / bf16s}
@@ -920,7 +924,7 @@ def main():
         line["rel_l2"] = err
         if not args.no_paths and args.path == "fft":
             paths.update(c3_paths(pkg, xs_d, xs_host, specs, stream, max(3, args.steps // 4),
-                                  ("gemm_bf16x3", "gemm_bf16x3_dense", "gemm_f32")))
+                                  ("gemm_bf16x3", "gemm_bf16x3_dense", "gemm_bf16x3_dense_2pass", "gemm_f32")))
         line["paths"] = paths
 
         if not args.no_e2e:

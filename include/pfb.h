@@ -282,7 +282,20 @@ PFB_API pfb_status pfb_batch_destroy(pfb_batch_t batch);
  * pfb_plan_autotune) or from a built-in default. */
 PFB_API int32_t pfb_plan_num_variants(pfb_plan_t plan);
 PFB_API int32_t pfb_plan_variant(pfb_plan_t plan);
-/* Select a variant explicitly (0 <= variant < pfb_plan_num_variants). */
+/* Select a variant explicitly (0 <= variant < pfb_plan_num_variants);
+ * PFB_ERR_UNSUPPORTED if the variant has no kernel for the plan's P and T.
+ * Variants: FP32 FFT path, P <= 1024: 0-4 tile shapes of the fused kernel,
+ * 5 warp-specialised; P = 2048, 4096: 0 synchronous cluster kernel, 1 and 2
+ * warp-specialised cluster kernels, 3 (P = 4096) the four-step 64 x 64
+ * cluster kernel.  Split-bf16 path: 0 the fused dense DFT-matrix product,
+ * 1 the factored (four-step) tensor-core DFT, 2 (P = 1024, 2048, 4096,
+ * T <= 16) the dense product in two passes -- the FIR into a plan-owned
+ * workspace of 4 * P bytes per spectrum (rounded up to 128-spectrum tiles per
+ * stream), then a pipelined tcgen05 GEMM.  The workspace grows on demand
+ * inside pfb_execute / pfb_execute_batch (PFB_ERR_OOM if it cannot), so
+ * launches of one plan in that variant must not overlap on different
+ * streams, and a CUDA graph of it must be captured after a first launch of
+ * the same size. */
 PFB_API pfb_status pfb_plan_set_variant(pfb_plan_t plan, int32_t variant);
 /* Time every variant on an input of n_samples (device scratch buffers the
  * call allocates, fills and frees; it synchronises cuda_stream), keep the

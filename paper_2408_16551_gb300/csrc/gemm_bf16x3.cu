@@ -62,6 +62,7 @@ constexpr uint32_t K2_IDESC = tc_idesc_bf16(K2_M, K2_N);
 int64_t cluster_units(int64_t S);
 
 int64_t gemm_bf16x3_units(const Plan &plan, int64_t S) {
+    if (plan.variant == 2) return gemm2p_units(plan, S);
     if (plan.variant == 1) return (plan.P == 1024 || ws_cluster_supported(plan)) ? S : cluster_units(S);
     return ((S + K2_M - 1) / K2_M) * (plan.P / (K2_N / 2));
 }
@@ -120,7 +121,8 @@ pfb_status build_gemm_f32_table(Plan &plan);
 
 // tables a variant needs that plan creation did not build
 pfb_status ensure_variant_tables(Plan &plan) {
-    if (plan.family == FAM_GEMM_BF16X3 && plan.variant == 0 && !plan.d_dft && plan.P >= K2_N / 2 && plan.T <= 16) {
+    if (plan.family == FAM_GEMM_BF16X3 && (plan.variant == 0 || plan.variant == 2) && !plan.d_dft &&
+        plan.P >= K2_N / 2 && plan.T <= 16) {
         pfb_status st = build_gemm_bf16x3_table(plan);
         if (st != PFB_OK) return st;
         PFB_CUDA_TRY(cudaDeviceSynchronize());
@@ -444,6 +446,7 @@ static pfb_status launch_k2_t(const Plan &plan, LaunchArgs &a, cudaStream_t stre
 
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     if (plan.variant == 1) return launch_gemm_bf16x3_tcf(plan, a, stream);
+    if (plan.variant == 2) return launch_gemm_bf16x3_2p(plan, a, stream);
     if (plan.P < K2_N / 2) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs P >= 128");
     if (plan.T > 16) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 DFT-GEMM path needs T <= 16");
     if (a.nunits > 0 && !plan.d_dft) return fail(PFB_ERR_INTERNAL, "split-bf16 DFT matrix not built");

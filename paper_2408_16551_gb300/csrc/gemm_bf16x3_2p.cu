@@ -1,0 +1,414 @@
+// Split-bf16 DFT-matrix product in two passes (variant 2 of the split-bf16
+// family, P = 1024, 2048, 4096, T <= 16): the literal DFT-as-GEMM of
+// Sec. 4.1 with the branch sums of Sec. 5.2 computed once.
+//
+// Pass 1 (k_fir_tiles, CUDA cores): the polyphase FIR for every spectrum,
+//   y[s,p] = sum_{m<T} h[m*P+p] x[(s+m)*P+p], split into bf16 hi = RN(y) and
+//   lo = RN(y - hi) and written to a workspace already in the tensor core's
+//   operand order: per 128-spectrum M tile and 64-real K block one 16 KB
+//   chunk of 8 x 8 core matrices (8 rows x 16 bytes each, K-major), so that
+//   pass 2 moves each operand with one bulk copy.
+// Pass 2 (k_gemm_tiles, tcgen05): X = [Yr|Yi] B with B the real block form of
+//   the DFT matrix (pre-tiled hi and lo, the table of variant 0), three
+//   products per K step (hi*hi + hi*lo + lo*hi), M = 128, N = 128, K = 16 per
+//   MMA, operands in shared memory, FP32 accumulation in TMEM.  One producer
+//   thread fills a 3-stage ring with four bulk copies per K block, one thread
+//   issues the MMAs, four epilogue warps drain the accumulator.  Accumulation
+//   is two-level as in variant 0: the tensor core sums chunks of 8 K blocks in
+//   one of two TMEM accumulators (double-buffered, so the MMAs continue while
+//   the other one is drained), and the epilogue adds every chunk into a
+//   running FP32 sum in registers (round to nearest); the tensor core's own
+//   accumulation drifts by about 1.8e-8 of the result per MMA step, which the
+//   chunking bounds independently of P.
+// Tiles run in blocks of 8 M tiles x 16 N tiles, so that the operand slabs
+// the grid works on at one time stay in L2.  Every wait is bounded (the
+// launch's wait_ns); on expiry the kernel records KERR_TIMEOUT, waits
+// (bounded) for what it issued and frees its TMEM.
+#include <cuda_bf16.h>
+
+#include "devutil.cuh"
+#include "internal.h"
+#include "sync.cuh"
+#include "tc.cuh"
+
+namespace pfb {
+
+constexpr int Y2_M = 128, Y2_KB = 64;                 // reals per workspace chunk: rows x K block
+constexpr int Y2_CHUNK_ELEMS = Y2_M * Y2_KB;          // bf16 elements per chunk (16 KB)
+constexpr int F2_THREADS = 256, F2_BR = 4;             // FIR pass: threads, branches per thread
+
+int64_t gemm2p_units(const Plan &plan, int64_t S) { return ((S + Y2_M - 1) / Y2_M) * (plan.P / 64); }
+
+bool gemm2p_supported(const Plan &plan) {
+    return (plan.P == 1024 || plan.P == 2048 || plan.P == 4096) && plan.T <= 16 &&
+           (plan.TT == 4 || plan.TT == 8 || plan.TT == 16);
+}
+
+// four consecutive branches p0 .. p0+3 of frame f as complex fp32 (zero past the end)
+template <int IN>
+__device__ __forceinline__ void load4(const StreamDesc &d, int64_t f, int P, int p0, float2 (&v)[4]) {
+    if (f >= d.n_frames) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = make_float2(0.f, 0.f);
+        return;
+    }
+    int64_t smp;
+    const void *src = frame_source(d, f, P, smp);
+    smp += p0;
+    if constexpr (IN == PFB_IN_C64) {
+        const float4 *q = reinterpret_cast<const float4 *>(static_cast<const float2 *>(src) + smp);
+        const float4 a = __ldg(q), b = __ldg(q + 1);
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(b.x, b.y);
+        v[3] = make_float2(b.z, b.w);
+    } else if constexpr (IN == PFB_IN_R32) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(src) + smp));
+        v[0] = make_float2(a.x, 0.f);
+        v[1] = make_float2(a.y, 0.f);
+        v[2] = make_float2(a.z, 0.f);
+        v[3] = make_float2(a.w, 0.f);
+    } else {
+        const int2 a = __ldg(reinterpret_cast<const int2 *>(static_cast<const char2 *>(src) + smp));
+        const char4 lo = *reinterpret_cast<const char4 *>(&a.x), hi = *reinterpret_cast<const char4 *>(&a.y);
+        const float sc = d.scale;
+        v[0] = make_float2((float)lo.x * sc, (float)lo.y * sc);
+        v[1] = make_float2((float)lo.z * sc, (float)lo.w * sc);
+        v[2] = make_float2((float)hi.x * sc, (float)hi.y * sc);
+        v[3] = make_float2((float)hi.z * sc, (float)hi.w * sc);
+    }
+}
+
+// Pass 1: work item w = (global M tile, chunk of 1024 branches); thread t owns
+// branches chunk * 1024 + 4t .. + 3 and streams the tile's 128 + T - 1 frames
+// through T pending sums per branch, registers only.
+template <int IN, int TT>
+__global__ void __launch_bounds__(F2_THREADS, 1)
+    k_fir_tiles(const __grid_constant__ LaunchArgs a, int P, int64_t ntiles, __nv_bfloat16 *yhi, __nv_bfloat16 *ylo) {
+    const int nchunk = P / (F2_THREADS * F2_BR), NTL = P / 64, KBLK = 2 * P / Y2_KB;
+    const int t = threadIdx.x;
+    for (int64_t w = blockIdx.x; w < ntiles * nchunk; w += gridDim.x) {
+        const int64_t gmt = w / nchunk;
+        const int chunk = (int)(w % nchunk);
+        const int si = find_stream(a, gmt * NTL);
+        const StreamDesc &d = a.s[si];
+        const int64_t s0 = (gmt - d.unit0 / NTL) * Y2_M;  // first spectrum of the tile in its stream
+        const int p0 = chunk * (F2_THREADS * F2_BR) + F2_BR * t;
+        float h[TT][4];
+#pragma unroll
+        for (int m = 0; m < TT; ++m)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) h[m][j] = __ldg(d.taps + m * P + p0 + j);
+        // this thread's 16 bytes of every row: K index 2 p0 .. 2 p0 + 7
+        const int kk0 = 2 * p0, kb = kk0 / Y2_KB, kg = (kk0 % Y2_KB) / 8;
+        const int64_t cbase = (gmt * KBLK + kb) * (int64_t)Y2_CHUNK_ELEMS + kg * 64;
+        float2 pend[TT][4];
+        constexpr int NFR = Y2_M + TT - 1;
+        for (int i0 = 0; i0 < NFR; i0 += TT) {
+#pragma unroll
+            for (int k = 0; k < TT; ++k) {
+                const int i = i0 + k;
+                if (i < NFR) {
+                    float2 v[4];
+                    load4<IN>(d, s0 + i, P, p0, v);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
+#pragma unroll
+                    for (int m = 1; m < TT; ++m) {
+                        const int js = ((k - m) % TT + TT) % TT;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
+                    }
+                    const int r = i - (TT - 1);  // row of the tile completed by this frame
+                    if (r >= 0) {
+                        const int js = (k + 1) % TT;
+                        uint4 hv, lv;
+                        split_bf16x2(pend[js][0], hv.x, lv.x);
+                        split_bf16x2(pend[js][1], hv.y, lv.y);
+                        split_bf16x2(pend[js][2], hv.z, lv.z);
+                        split_bf16x2(pend[js][3], hv.w, lv.w);
+                        const int64_t off = cbase + (r >> 3) * 512 + (r & 7) * 8;  // core matrix (r/8, kg), row r%8
+                        *reinterpret_cast<uint4 *>(yhi + off) = hv;
+                        *reinterpret_cast<uint4 *>(ylo + off) = lv;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: the product
+// ---------------------------------------------------------------------------
+constexpr int G2_N = 128;                              // reals per N tile (64 bins)
+constexpr int G2_NST = 3;                              // ring stages
+constexpr int G2_CHUNK = 8;                            // K blocks per TMEM accumulation chunk
+constexpr int G2_OPB = Y2_CHUNK_ELEMS * 2;             // bytes of one operand chunk (A: 128 x 64, B: 128 x 64)
+constexpr int G2_STAGE = 4 * G2_OPB;                   // A hi, A lo, B hi, B lo
+constexpr int G2_EPIW = 4, G2_PRODW = 4, G2_MMAW = 5, G2_THREADS = 6 * 32;
+constexpr int G2_SMEM = G2_NST * G2_STAGE + 256 + 1024;  // + barriers, + alignment slack
+constexpr uint32_t G2_TMEM_COLS = 256;                 // two 128-column accumulators
+constexpr uint32_t G2_IDESC = tc_idesc_bf16(128, G2_N);
+constexpr int G2_MB = 8, G2_NB = 16;                   // tile blocks kept together (L2)
+
+// tile w of the blocked order -> (global M tile, N tile)
+__device__ __forceinline__ void g2_tile(int64_t w, int64_t ntm, int ntn, int64_t &gmt, int &nt) {
+    const int nb = ntn < G2_NB ? ntn : G2_NB;
+    const int64_t bm = w / ((int64_t)G2_MB * ntn);
+    const int64_t idx = w - bm * G2_MB * ntn;
+    const int64_t mrows = min((int64_t)G2_MB, ntm - bm * G2_MB);
+    const int64_t bn = idx / (mrows * nb), r = idx % (mrows * nb);
+    gmt = bm * G2_MB + r / nb;
+    nt = (int)(bn * nb + r % nb);
+}
+
+__global__ void __launch_bounds__(G2_THREADS, 1)
+    k_gemm_tiles(const __grid_constant__ LaunchArgs a, int P, int64_t ntm, const __nv_bfloat16 *yhi,
+                 const __nv_bfloat16 *ylo) {
+    extern __shared__ __align__(1024) uint8_t g2_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(g2_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + G2_NST * G2_STAGE);
+    // full[3], empty[3], dfull[2], dfree[2], then the TMEM address and the abort flag
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[G2_NST]);
+    const uint32_t dfull0 = smem_u32(&bars[2 * G2_NST]), dfree0 = smem_u32(&bars[2 * G2_NST + 2]);
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(bars + 2 * G2_NST + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * G2_NST + 5);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t wns = a.wait_ns;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < G2_NST; ++i) {
+            mbar_init(full0 + 8 * i, 1);   // the producer's arrive.expect_tx + the copies' bytes
+            mbar_init(empty0 + 8 * i, 1);  // the MMA thread's commit
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(dfull0 + 8 * i, 1);         // the MMA thread's commit at the end of a chunk
+            mbar_init(dfree0 + 8 * i, G2_EPIW);   // every epilogue warp has read the accumulator
+        }
+        mbar_init_fence();
+        *abort_flag = 0;
+    }
+    if (warp == G2_MMAW) tmem_alloc(smem_u32((const void *)tmem_slot), G2_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int ntn = P / 64, KBLK = 2 * P / Y2_KB;
+    const int nchunks = (KBLK + G2_CHUNK - 1) / G2_CHUNK;
+    const int64_t ntiles = ntm * ntn;
+    const __nv_bfloat16 *Bhi = static_cast<const __nv_bfloat16 *>(a.aux);
+    // the variant-0 table: tiles (N tile of 256 reals, K block) of 256 x 64; an N tile
+    // of 128 reals is one contiguous half of one of them
+    const __nv_bfloat16 *Blo = Bhi + (int64_t)(P / 128) * KBLK * (2 * Y2_CHUNK_ELEMS);
+    const uint32_t sA = smem_u32(sm);
+
+    if (warp == G2_PRODW) {
+        // ---------------- producer: four bulk copies per K block ----------------
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < ntiles && ok; w += gridDim.x) {
+                int64_t gmt;
+                int nt;
+                g2_tile(w, ntm, ntn, gmt, nt);
+                for (int kb = 0; kb < KBLK; ++kb, ++g) {
+                    const uint32_t st = g % G2_NST;
+                    if (g >= G2_NST && !mbar_wait(empty0 + 8 * st, ((g / G2_NST) + 1) & 1, wns)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = full0 + 8 * st, dst = sA + st * G2_STAGE;
+                    mbar_expect_tx(fb, G2_STAGE);
+                    const int64_t ao = (gmt * KBLK + kb) * (int64_t)Y2_CHUNK_ELEMS;
+                    const int64_t bo = ((int64_t)(nt >> 1) * KBLK + kb) * (2 * Y2_CHUNK_ELEMS) + (nt & 1) * Y2_CHUNK_ELEMS;
+                    bulk_g2s(dst, yhi + ao, G2_OPB, fb);
+                    bulk_g2s(dst + G2_OPB, ylo + ao, G2_OPB, fb);
+                    bulk_g2s(dst + 2 * G2_OPB, Bhi + bo, G2_OPB, fb);
+                    bulk_g2s(dst + 3 * G2_OPB, Blo + bo, G2_OPB, fb);
+                }
+            }
+            if (!ok) *abort_flag = 1;
+            // every copy issued has landed before the CTA exits
+            const uint32_t first = g > G2_NST ? g - G2_NST : 0;
+            for (uint32_t q = first; q < g; ++q)
+                if (!mbar_wait(full0 + 8 * (q % G2_NST), (q / G2_NST) & 1, wns)) *abort_flag = 1;
+        }
+        __syncwarp();
+    } else if (warp == G2_MMAW) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t g = 0, c = 0;
+            bool ok = true, issued = false;
+            for (int64_t w = blockIdx.x; w < ntiles && ok; w += gridDim.x) {
+                for (int kb = 0; kb < KBLK && ok; ++kb, ++g) {
+                    const uint32_t buf = c & 1;
+                    if (kb % G2_CHUNK == 0 && c >= 2 && !mbar_wait(dfree0 + 8 * buf, ((c >> 1) + 1) & 1, wns)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = g % G2_NST;
+                    if (!mbar_wait(full0 + 8 * st, (g / G2_NST) & 1, wns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_t = tmem + buf * G2_N;
+                    const uint32_t ah = sA + st * G2_STAGE, al = ah + G2_OPB, bh = ah + 2 * G2_OPB, bl = ah + 3 * G2_OPB;
+#pragma unroll
+                    for (int ks = 0; ks < Y2_KB / 16; ++ks) {
+                        const uint64_t dah = tc_desc_kmajor(ah + ks * 256, 128, 1024);
+                        const uint64_t dal = tc_desc_kmajor(al + ks * 256, 128, 1024);
+                        const uint64_t dbh = tc_desc_kmajor(bh + ks * 256, 128, 1024);
+                        const uint64_t dbl = tc_desc_kmajor(bl + ks * 256, 128, 1024);
+                        tc_mma_ss(d_t, dah, dbh, G2_IDESC, (kb % G2_CHUNK > 0 || ks > 0) ? 1u : 0u);
+                        tc_mma_ss(d_t, dah, dbl, G2_IDESC, 1u);
+                        tc_mma_ss(d_t, dal, dbh, G2_IDESC, 1u);
+                    }
+                    tc_commit(empty0 + 8 * st);  // the stage is free once these MMAs are done
+                    issued = true;
+                    if (kb % G2_CHUNK == G2_CHUNK - 1 || kb == KBLK - 1) {
+                        tc_commit(dfull0 + 8 * buf);  // the chunk's sum is in the accumulator
+                        ++c;
+                    }
+                }
+            }
+            if (!ok) *abort_flag = 1;
+            // every MMA issued has completed before TMEM is freed
+            if (issued && !ok) {
+                const uint32_t gl = g - 1;
+                if (!mbar_wait(empty0 + 8 * (gl % G2_NST), (gl / G2_NST) & 1, wns)) *abort_flag = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps: TMEM lane quarter = warp ----------------
+        float sacc[G2_N];
+        uint32_t c = 0;
+        bool ok = true;
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int64_t w = blockIdx.x; w < ntiles && ok; w += gridDim.x) {
+            int64_t gmt;
+            int nt;
+            g2_tile(w, ntm, ntn, gmt, nt);
+#pragma unroll
+            for (int i = 0; i < G2_N; ++i) sacc[i] = 0.f;
+            for (int cc = 0; cc < nchunks; ++cc, ++c) {
+                const uint32_t buf = c & 1;
+                if (!__all_sync(0xffffffffu, mbar_wait(dfull0 + 8 * buf, (c >> 1) & 1, wns))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int q = 0; q < G2_N / 32; ++q) {
+                    uint32_t r[32];
+                    tmem_ld32(trow + buf * G2_N + 32 * q, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sacc[32 * q + i] += __uint_as_float(r[i]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(dfree0 + 8 * buf);
+            }
+            if (!ok) break;
+            const int si = find_stream(a, gmt * ntn);
+            const StreamDesc &d = a.s[si];
+            const int64_t s = (gmt - d.unit0 / ntn) * Y2_M + 32 * warp + lane;
+            if (s < d.S) {
+                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(d.out) + s * 2 * d.ldo + (int64_t)nt * G2_N);
+#pragma unroll
+                for (int i = 0; i < G2_N / 4; ++i)
+                    __stcs(o + i, make_float4(sacc[4 * i], sacc[4 * i + 1], sacc[4 * i + 2], sacc[4 * i + 3]));
+            }
+        }
+        if (!ok) *abort_flag = 1;
+    }
+    // ---------------- teardown ----------------
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == G2_MMAW) tmem_dealloc(tmem, G2_TMEM_COLS);
+    if (threadIdx.x == 0 && *abort_flag) report_error(a.err, KERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// launch: workspace, pass 1, pass 2 (same stream)
+// ---------------------------------------------------------------------------
+template <int IN, int TT>
+static pfb_status launch_fir_tiles(const Plan &plan, const LaunchArgs &a, int64_t ntm, __nv_bfloat16 *yhi,
+                                   __nv_bfloat16 *ylo, cudaStream_t stream) {
+    const int64_t work = ntm * (plan.P / (F2_THREADS * F2_BR));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = work < 4 * (int64_t)sms ? work : 4 * (int64_t)sms;
+    k_fir_tiles<IN, TT><<<(unsigned)grid, F2_THREADS, 0, stream>>>(a, plan.P, ntm, yhi, ylo);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PFB_OK : cuda_fail(e, "launch k_fir_tiles");
+}
+
+template <int IN>
+static pfb_status launch_fir_tiles_t(const Plan &plan, const LaunchArgs &a, int64_t ntm, __nv_bfloat16 *yhi,
+                                     __nv_bfloat16 *ylo, cudaStream_t stream) {
+    switch (plan.TT) {
+    case 4: return launch_fir_tiles<IN, 4>(plan, a, ntm, yhi, ylo, stream);
+    case 8: return launch_fir_tiles<IN, 8>(plan, a, ntm, yhi, ylo, stream);
+    default: return launch_fir_tiles<IN, 16>(plan, a, ntm, yhi, ylo, stream);
+    }
+}
+
+// The workspace (hi and lo branch sums, 4 x P bytes per padded spectrum) is
+// the plan's and grows on demand: launches of one plan in this variant must
+// not overlap, and the first launch of a size must come before any CUDA-graph
+// capture of it.
+pfb_status launch_gemm_bf16x3_2p(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
+    if (!gemm2p_supported(plan)) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 variant 2 needs P in {1024, 2048, 4096}, T <= 16");
+    if (a.nunits <= 0) return PFB_OK;
+    if (!plan.d_dft) return fail(PFB_ERR_INTERNAL, "split-bf16 DFT matrix not built");
+    const int ntn = plan.P / 64;
+    const int64_t ntm = a.nunits / ntn;
+    const size_t half = (size_t)ntm * (2 * plan.P / Y2_KB) * Y2_CHUNK_ELEMS * sizeof(__nv_bfloat16);
+    Plan &mp = const_cast<Plan &>(plan);
+    {
+        std::lock_guard<std::mutex> lk(mp.stage_mu);
+        if (mp.ws2_bytes < 2 * half) {
+            cudaFree(mp.d_ws2);
+            mp.d_ws2 = nullptr;
+            mp.ws2_bytes = 0;
+            if (cudaMalloc(&mp.d_ws2, 2 * half) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(PFB_ERR_OOM, "split-bf16 variant 2 workspace");
+            }
+            mp.ws2_bytes = 2 * half;
+        }
+    }
+    __nv_bfloat16 *yhi = static_cast<__nv_bfloat16 *>(mp.d_ws2);
+    __nv_bfloat16 *ylo = yhi + half / sizeof(__nv_bfloat16);
+    pfb_status st;
+    switch (plan.in_dtype) {
+    case PFB_IN_C64: st = launch_fir_tiles_t<PFB_IN_C64>(plan, a, ntm, yhi, ylo, stream); break;
+    case PFB_IN_R32: st = launch_fir_tiles_t<PFB_IN_R32>(plan, a, ntm, yhi, ylo, stream); break;
+    case PFB_IN_CI8: st = launch_fir_tiles_t<PFB_IN_CI8>(plan, a, ntm, yhi, ylo, stream); break;
+    default: return fail(PFB_ERR_INVALID, "bad dtype");
+    }
+    if (st != PFB_OK) return st;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, G2_SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gemm_tiles)");
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = sms;  // one CTA per SM (198 KB of shared memory)
+    }
+    const int64_t ntiles = ntm * ntn;
+    const int64_t grid = ntiles < grid_cap ? ntiles : grid_cap;
+    k_gemm_tiles<<<(unsigned)grid, G2_THREADS, G2_SMEM, stream>>>(a, plan.P, ntm, yhi, ylo);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PFB_OK : cuda_fail(e, "launch k_gemm_tiles");
+}
+
+}  // namespace pfb

@@ -122,6 +122,9 @@ struct Plan {
     // y~ [S][P] and (split-bf16 plans) the internal one-tap inverse plan
     void *d_synth_y = nullptr;
     size_t synth_y_bytes = 0;
+    // split-bf16 variant 2: the pre-tiled hi/lo branch sums (grown on demand by the launch)
+    mutable void *d_ws2 = nullptr;
+    mutable size_t ws2_bytes = 0;
     Plan *inv = nullptr;
     // host staging for pfb_execute_host
     std::mutex stage_mu;
@@ -166,6 +169,9 @@ pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &args, cudaStream_t stre
 pfb_status launch_fft_generic(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+pfb_status launch_gemm_bf16x3_2p(const Plan &plan, LaunchArgs &args, cudaStream_t stream);  // variant 2
+int64_t gemm2p_units(const Plan &plan, int64_t S);
+bool gemm2p_supported(const Plan &plan);
 pfb_status launch_gemm_bf16x3_tcf(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 bool tcf_supported(const Plan &plan);
 pfb_status build_tcf_table(Plan &plan);

@@ -182,6 +182,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
     cudaFree(p->d_synth_y);
+    cudaFree(p->d_ws2);
     free_inverse_plan(*p);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;

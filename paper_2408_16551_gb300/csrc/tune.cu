@@ -76,13 +76,14 @@ static void save_file_cache() {
 }
 
 // fast FFT family: 6 tile shapes; split-bf16 family: 0 = dense DFT-matrix
-// product, 1 = factored (four-step) tensor-core DFT; cluster FFT family:
+// product, 1 = factored (four-step) tensor-core DFT, 2 = dense product in two
+// passes (FIR to a pre-tiled workspace, then a pipelined tcgen05 GEMM); cluster FFT family:
 // 0 = synchronous, 1 = warp-specialised with the cross-CTA step in the FFT
 // warps, 2 = warp-specialised with one exchange from the FIR warps' radix-4
 // step to the receiving FFT warps, 3 = four-step 64 x 64 (P = 4096)
 int family_variants(const Plan &plan) {
     if (plan.family == FAM_FFT_FAST) return 6;
-    if (plan.family == FAM_GEMM_BF16X3) return 2;
+    if (plan.family == FAM_GEMM_BF16X3) return 3;
     if (plan.family == FAM_FFT_CLUSTER) return 4;
     return 1;
 }
@@ -92,6 +93,7 @@ int family_variants(const Plan &plan) {
 static bool variant_supported(const Plan &plan, int v) {
     if (plan.family == FAM_FFT_FAST && v == 5) return plan.P >= 128 && plan.T == plan.TT;
     if (plan.family == FAM_GEMM_BF16X3 && v == 1) return tcf_supported(plan);
+    if (plan.family == FAM_GEMM_BF16X3 && v == 2) return gemm2p_supported(plan);
     if (plan.family == FAM_FFT_CLUSTER && v == 3) return wcf_supported(plan);
     if (plan.family == FAM_FFT_CLUSTER && v >= 1) return v < 3 && ws_cluster_supported(plan);
     return v >= 0 && v < family_variants(plan);

@@ -132,7 +132,7 @@ def test_gemm_paths_report_unsupported_shapes():
 
 def test_factored_is_the_default_at_p1024():
     plan = pkg.Plan(1024, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
-    assert plan.num_variants == 2 and plan.variant == 1
+    assert plan.num_variants == 3 and plan.variant == 1
     plan2 = pkg.Plan(1024, 12, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
     assert plan2.variant == 0                 # T = 12 is not a compiled tap count
     with pytest.raises(pkg.PFBError):
@@ -251,3 +251,72 @@ def test_gemm_bf16x3_ws_cluster_repeatable_and_matches_split_model(P, T, dt, row
         assert torch.equal(plan.execute(xd), first)
     ref = reference(x, dt, P, T, synth.WIN_BLACKMAN)
     assert_close(first.cpu().numpy(), ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"ws cluster tc P={P} T={T}")
+
+
+# ---------------------------------------------------------------------------
+# dense product in two passes, variant 2 (FIR to a pre-tiled workspace, then a
+# pipelined tcgen05 GEMM with double-buffered TMEM accumulators)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("P,T,dt,rows", [(1024, 16, synth.IN_C64, 128 * 2 + 45), (2048, 8, synth.IN_CI8, 128 + 1),
+                                         (4096, 16, synth.IN_C64, 127), (4096, 4, synth.IN_R32, 129),
+                                         (1024, 12, synth.IN_C64, 3)])
+def test_gemm_bf16x3_two_pass_parity(P, T, dt, rows):
+    """Ragged last M tiles (S not a multiple of 128), every input type, T
+    padded to its compiled tap count (T = 12 runs with TT = 16)."""
+    n = P * (T - 1 + rows) + 7
+    plan, x, got = _run_variant(2, P, T, dt, n, seed=P + 3 * T + rows)
+    assert plan.variant == 2
+    ref = reference(x, dt, P, T, synth.WIN_HANN)
+    assert got.shape == ref.shape
+    e2, em = assert_close(got, ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"bf16x3 two-pass P={P} T={T} rows={rows}")
+    assert e2 > 1e-8
+    assert plan.status() == pkg.PFB_OK
+
+
+def test_gemm_bf16x3_two_pass_matches_split_model_and_dense():
+    """Against the FP64 model of the split arithmetic (indexing errors would be
+    O(1)), and against the fused dense variant 0 (same products, same chunked
+    accumulation: the two agree to the accumulation error)."""
+    P, T = 1024, 16
+    n = P * (T - 1 + 300)
+    plan, x, got = _run_variant(2, P, T, synth.IN_C64, n, seed=21)
+    h = oracle.prototype(P, T, oracle.WIN_HANN)
+    y = oracle.fir(oracle.dequant(x, oracle.IN_C64), P, T, h)
+    model = split_bf16x3_model(y.astype(np.complex64), P)
+    assert oracle.rel_l2(got, model) < 3e-6
+    plan0, _, got0 = _run_variant(0, P, T, synth.IN_C64, n, seed=21)
+    assert oracle.rel_l2(got, got0) < 3e-6
+
+
+def test_gemm_bf16x3_two_pass_batch_repeatable():
+    """Uneven streams (one with 0 spectra, one of a single spectrum) in one
+    batched launch: equal to per-stream launches, bitwise repeatable, and the
+    workspace grows between calls of different sizes."""
+    import torch
+    P, T = 4096, 16
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_BLACKMAN, pkg.PFB_DFT_GEMM_BF16X3)
+    plan.variant = 2
+    lens = [P * (T - 1 + 200) + 3, P * 3, P * (T - 1 + 1), P * (T - 1 + 257)]
+    xs = [to_device(synth.small_stream(P, T, n, seed=40 + i).generate()) for i, n in enumerate(lens)]
+    singles = [plan.execute(x).clone() if plan.out_spectra(x.numel()) > 0 else None for x in xs]
+    outs = [torch.full((max(plan.out_spectra(x.numel()), 1), P), 7.0, dtype=torch.complex64, device="cuda") for x in xs]
+    for _ in range(3):
+        pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xs, outs)])
+        torch.cuda.synchronize()
+        for s, o in zip(singles, outs):
+            if s is not None:
+                assert torch.equal(o[:s.shape[0]], s)
+            else:
+                assert torch.all(o == 7.0)
+    assert plan.status() == pkg.PFB_OK
+    x3 = synth.small_stream(P, T, lens[3], seed=43).generate()
+    ref = reference(x3, synth.IN_C64, P, T, synth.WIN_BLACKMAN, s0=250, ns=7)
+    assert_close(outs[3][250:257].cpu().numpy(), ref, TOL_BF16X3, TOL_MAX_BF16X3, what="two-pass batch stream 3")
+
+
+def test_gemm_bf16x3_two_pass_unsupported():
+    plan = pkg.Plan(512, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan.num_variants == 3
+    with pytest.raises(pkg.PFBError):
+        plan.variant = 2
