@@ -268,9 +268,11 @@ def c3_config(path, P, T, nstreams, n, spectra):
     """The headline workload's config; both arms print exactly this dict."""
     return {"workload": C3_WORKLOAD + "; one pfb_execute_batch over all streams per step, "
                         + {"fft": "FIR + FFT path (FP32)", "bf16x3": "FIR + factored split-bf16 tensor-core DFT",
-                           "bf16x3_dense": "FIR + dense split-bf16 DFT-matrix GEMM"}[path],
+                           "bf16x3_dense": "FIR + dense split-bf16 DFT-matrix GEMM",
+                           "bf16x3_dense_2pass": "FIR pass + pipelined dense split-bf16 DFT-matrix GEMM"}[path],
             "P": P, "T": T, "streams": nstreams, "n_samples": n, "spectra": spectra,
-            "path": {"fft": "fft_f32", "bf16x3": "gemm_bf16x3", "bf16x3_dense": "gemm_bf16x3_dense"}[path],
+            "path": {"fft": "fft_f32", "bf16x3": "gemm_bf16x3", "bf16x3_dense": "gemm_bf16x3_dense",
+                     "bf16x3_dense_2pass": "gemm_bf16x3_dense_2pass"}[path],
             "l2": f"inputs larger than L2: each step reads {n * 8 >> 20} MiB and writes "
                   f"{spectra * P * 8 >> 20} MiB (> 129 MB L2); no flush between steps",
             "replicas": "each rank channelises its own copy of the workload (weak scaling, no collective)"}
@@ -765,7 +767,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=20000)
     ap.add_argument("--no-configs", action="store_true", help="skip the c2/c4/oversampled/synthesis lines")
     ap.add_argument("--minimal", action="store_true", help="headline timing only (for profiler runs)")
-    ap.add_argument("--path", default="fft", choices=["fft", "bf16x3", "bf16x3_dense"],
+    ap.add_argument("--path", default="fft", choices=["fft", "bf16x3", "bf16x3_dense", "bf16x3_dense_2pass"],
                     help="DFT route of the headline step (profiler runs): FP32 FFT, factored split-bf16 "
                          "tensor-core DFT, or the dense split-bf16 DFT-matrix product")
     ap.add_argument("--streams", type=int, default=64, help="c3 streams of the headline step (profiler runs)")
@@ -825,7 +827,8 @@ def main():
     n_stream = int(xs_host[0].size)
     n = n_stream * len(xs_host)
     route = {"fft": (pkg.PFB_DFT_FFT_F32, None), "bf16x3": (pkg.PFB_DFT_GEMM_BF16X3, 1),
-             "bf16x3_dense": (pkg.PFB_DFT_GEMM_BF16X3, 0)}[args.path]
+             "bf16x3_dense": (pkg.PFB_DFT_GEMM_BF16X3, 0),
+             "bf16x3_dense_2pass": (pkg.PFB_DFT_GEMM_BF16X3, 2)}[args.path]
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, win, route[0])
     if route[1] is not None:
         plan.variant = route[1]

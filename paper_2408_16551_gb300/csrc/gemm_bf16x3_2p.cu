@@ -374,6 +374,9 @@ pfb_status launch_gemm_bf16x3_2p(const Plan &plan, LaunchArgs &a, cudaStream_t s
     {
         std::lock_guard<std::mutex> lk(mp.stage_mu);
         if (mp.ws2_bytes < 2 * half) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+                return fail(PFB_ERR_UNSUPPORTED, "split-bf16 variant 2: run a launch of this size before capturing it");
             cudaFree(mp.d_ws2);
             mp.d_ws2 = nullptr;
             mp.ws2_bytes = 0;

@@ -101,7 +101,7 @@ static bool variant_supported(const Plan &plan, int v) {
 
 int default_variant(const Plan &plan) {
     if (family_variants(plan) <= 1) return 0;
-    if (plan.family == FAM_GEMM_BF16X3) return tcf_supported(plan) ? 1 : 0;
+    if (plan.family == FAM_GEMM_BF16X3) return tcf_supported(plan) ? 1 : gemm2p_supported(plan) ? 2 : 0;
     if (plan.family == FAM_FFT_CLUSTER) return wcf_supported(plan) ? 3 : ws_cluster_supported(plan) ? 2 : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_file_cache();

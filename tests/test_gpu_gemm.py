@@ -134,7 +134,7 @@ def test_factored_is_the_default_at_p1024():
     plan = pkg.Plan(1024, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
     assert plan.num_variants == 3 and plan.variant == 1
     plan2 = pkg.Plan(1024, 12, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
-    assert plan2.variant == 0                 # T = 12 is not a compiled tap count
+    assert plan2.variant == 2                 # T = 12 is not a compiled tap count: the two-pass product
     with pytest.raises(pkg.PFBError):
         plan2.variant = 1
     plan3 = pkg.Plan(512, 16, pkg.PFB_IN_C64, pkg.PFB_WIN_HANN, pkg.PFB_DFT_GEMM_BF16X3)
