@@ -253,6 +253,33 @@ def test_gemm_bf16x3_ws_cluster_repeatable_and_matches_split_model(P, T, dt, row
     assert_close(first.cpu().numpy(), ref, TOL_BF16X3, TOL_MAX_BF16X3, what=f"ws cluster tc P={P} T={T}")
 
 
+def test_gemm_bf16x3_factored_p4096_batch_equals_single():
+    """P = 4096 (the four-step 64 x 64 cluster kernel with its 16-point DFT steps
+    on the tensor cores): uneven streams, one with no spectrum and one with a
+    single spectrum (partial batches), in one launch equal to per-stream
+    launches, and bitwise repeatable."""
+    import torch
+    P, T = 4096, 16
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HAMMING, pkg.PFB_DFT_GEMM_BF16X3)
+    assert plan.variant == 1
+    lens = [P * 20 + 3, P * 3, P * 16, P * 97 + 11, P * 300, P * 41]
+    xs = [to_device(synth.small_stream(P, T, n, seed=90 + i).generate()) for i, n in enumerate(lens)]
+    singles = [plan.execute(x).clone() if plan.out_spectra(x.numel()) > 0 else None for x in xs]
+    outs = [torch.full((max(plan.out_spectra(x.numel()), 1), P), 5.0, dtype=torch.complex64, device="cuda") for x in xs]
+    for _ in range(3):
+        pkg.pfb_execute_batch([(plan, x, o) for x, o in zip(xs, outs)])
+        torch.cuda.synchronize()
+        for sgl, o in zip(singles, outs):
+            if sgl is not None:
+                assert torch.equal(o[:sgl.shape[0]], sgl)
+            else:
+                assert torch.all(o == 5.0)
+    assert plan.status() == pkg.PFB_OK
+    x4 = synth.small_stream(P, T, lens[4], seed=94).generate()
+    ref = reference(x4, synth.IN_C64, P, T, synth.WIN_HAMMING, s0=100, ns=5)
+    assert_close(outs[4][100:105].cpu().numpy(), ref, TOL_BF16X3, TOL_MAX_BF16X3, what="factored P=4096 batch")
+
+
 # ---------------------------------------------------------------------------
 # dense product in two passes, variant 2 (FIR to a pre-tiled workspace, then a
 # pipelined tcgen05 GEMM with double-buffered TMEM accumulators)
