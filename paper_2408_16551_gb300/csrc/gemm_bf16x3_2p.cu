@@ -2,7 +2,7 @@
 // family, P = 1024, 2048, 4096, T <= 16): the literal DFT-as-GEMM of
 // Sec. 4.1 with the branch sums of Sec. 5.2 computed once.
 //
-// Pass 1 (k_fir_tiles, CUDA cores): the polyphase FIR for every spectrum,
+// Pass 1 (k_fir_tiles_ring, CUDA cores): the polyphase FIR for every spectrum,
 //   y[s,p] = sum_{m<T} h[m*P+p] x[(s+m)*P+p], split into bf16 hi = RN(y) and
 //   lo = RN(y - hi) and written to a workspace already in the tensor core's
 //   operand order: per 128-spectrum M tile and 64-real K block one 16 KB
@@ -44,97 +44,170 @@ bool gemm2p_supported(const Plan &plan) {
            (plan.TT == 4 || plan.TT == 8 || plan.TT == 16);
 }
 
-// four consecutive branches p0 .. p0+3 of frame f as complex fp32 (zero past the end)
+// Pass 1: work item w = (global M tile, chunk of 1024 branches).  A producer
+// warpgroup gathers the item's 128 + T - 1 frame slices with 16-byte
+// asynchronous copies (one arrival per thread on the slot's barrier) into a
+// ring of R2_NSLOT slots; FIR thread t owns branches chunk * 1024 + 4t .. + 3
+// and streams the frames through T pending sums per branch in registers
+// (register split FIR 224 / producer 56).  Reading the frames straight from
+// global memory instead ran pass 1 about 2.7 % of the two passes slower.
+constexpr int R2_NSLOT = 8, R2_THREADS = F2_THREADS + 128;
 template <int IN>
-__device__ __forceinline__ void load4(const StreamDesc &d, int64_t f, int P, int p0, float2 (&v)[4]) {
-    if (f >= d.n_frames) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = make_float2(0.f, 0.f);
-        return;
-    }
-    int64_t smp;
-    const void *src = frame_source(d, f, P, smp);
-    smp += p0;
-    if constexpr (IN == PFB_IN_C64) {
-        const float4 *q = reinterpret_cast<const float4 *>(static_cast<const float2 *>(src) + smp);
-        const float4 a = __ldg(q), b = __ldg(q + 1);
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
-        v[2] = make_float2(b.x, b.y);
-        v[3] = make_float2(b.z, b.w);
-    } else if constexpr (IN == PFB_IN_R32) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(src) + smp));
-        v[0] = make_float2(a.x, 0.f);
-        v[1] = make_float2(a.y, 0.f);
-        v[2] = make_float2(a.z, 0.f);
-        v[3] = make_float2(a.w, 0.f);
-    } else {
-        const int2 a = __ldg(reinterpret_cast<const int2 *>(static_cast<const char2 *>(src) + smp));
-        const char4 lo = *reinterpret_cast<const char4 *>(&a.x), hi = *reinterpret_cast<const char4 *>(&a.y);
-        const float sc = d.scale;
-        v[0] = make_float2((float)lo.x * sc, (float)lo.y * sc);
-        v[1] = make_float2((float)lo.z * sc, (float)lo.w * sc);
-        v[2] = make_float2((float)hi.x * sc, (float)hi.y * sc);
-        v[3] = make_float2((float)hi.z * sc, (float)hi.w * sc);
-    }
-}
+struct R2Cfg {
+    static constexpr int ESZ = IN == PFB_IN_C64 ? 8 : (IN == PFB_IN_R32 ? 4 : 2);
+    static constexpr int FB = F2_THREADS * F2_BR * ESZ;  // bytes of the CTA's 1024 branches of a frame
+    static constexpr int NCP = FB / 16 / 128;            // 16-byte copies per producer thread and frame
+    static constexpr int SMEM = R2_NSLOT * FB + 2 * R2_NSLOT * 8 + 16;
+    static_assert(NCP * 16 * 128 == FB, "whole 16-byte pieces per producer thread");
+};
 
-// Pass 1: work item w = (global M tile, chunk of 1024 branches); thread t owns
-// branches chunk * 1024 + 4t .. + 3 and streams the tile's 128 + T - 1 frames
-// through T pending sums per branch, registers only.
 template <int IN, int TT>
-__global__ void __launch_bounds__(F2_THREADS, 1)
-    k_fir_tiles(const __grid_constant__ LaunchArgs a, int P, int64_t ntiles, __nv_bfloat16 *yhi, __nv_bfloat16 *ylo) {
+__global__ void __launch_bounds__(R2_THREADS, 1)
+    k_fir_tiles_ring(const __grid_constant__ LaunchArgs a, int P, int64_t ntiles, __nv_bfloat16 *yhi,
+                     __nv_bfloat16 *ylo) {
+    using C = R2Cfg<IN>;
+    extern __shared__ __align__(128) uint8_t r2_smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(r2_smem + R2_NSLOT * C::FB);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * R2_NSLOT);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[R2_NSLOT]);
     const int nchunk = P / (F2_THREADS * F2_BR), NTL = P / 64, KBLK = 2 * P / Y2_KB;
-    const int t = threadIdx.x;
-    for (int64_t w = blockIdx.x; w < ntiles * nchunk; w += gridDim.x) {
-        const int64_t gmt = w / nchunk;
-        const int chunk = (int)(w % nchunk);
-        const int si = find_stream(a, gmt * NTL);
-        const StreamDesc &d = a.s[si];
-        const int64_t s0 = (gmt - d.unit0 / NTL) * Y2_M;  // first spectrum of the tile in its stream
-        const int p0 = chunk * (F2_THREADS * F2_BR) + F2_BR * t;
-        float h[TT][4];
+    constexpr int NFR = Y2_M + TT - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t wns = (uint32_t)a.wait_ns;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < R2_NSLOT; ++i) {
+            mbar_init(full0 + 8 * i, 128);             // one copy-completion arrival per producer thread
+            mbar_init(empty0 + 8 * i, F2_THREADS / 32);  // every FIR warp has read the slot
+        }
+        mbar_init_fence();
+        *abort_flag = 0;
+    }
+    __syncthreads();
+    if (warp < F2_THREADS / 32) {
+        // ---------------- FIR warps ----------------
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
+        const int t = threadIdx.x;
+        uint32_t pc = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < ntiles * nchunk && ok; w += gridDim.x) {
+            const int64_t gmt = w / nchunk;
+            const int chunk = (int)(w % nchunk);
+            const int si = find_stream(a, gmt * NTL);
+            const StreamDesc &d = a.s[si];
+            const int p0 = chunk * (F2_THREADS * F2_BR) + F2_BR * t;
+            float h[TT][4];
 #pragma unroll
-        for (int m = 0; m < TT; ++m)
+            for (int m = 0; m < TT; ++m)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) h[m][j] = __ldg(d.taps + m * P + p0 + j);
-        // this thread's 16 bytes of every row: K index 2 p0 .. 2 p0 + 7
-        const int kk0 = 2 * p0, kb = kk0 / Y2_KB, kg = (kk0 % Y2_KB) / 8;
-        const int64_t cbase = (gmt * KBLK + kb) * (int64_t)Y2_CHUNK_ELEMS + kg * 64;
-        float2 pend[TT][4];
-        constexpr int NFR = Y2_M + TT - 1;
-        for (int i0 = 0; i0 < NFR; i0 += TT) {
+                for (int j = 0; j < 4; ++j) h[m][j] = __ldg(d.taps + m * P + p0 + j);
+            const int kk0 = 2 * p0, kb = kk0 / Y2_KB, kg = (kk0 % Y2_KB) / 8;
+            const int64_t cbase = (gmt * KBLK + kb) * (int64_t)Y2_CHUNK_ELEMS + kg * 64;
+            const float sc = d.scale;
+            float2 pend[TT][4];
+            for (int i0 = 0; i0 < NFR && ok; i0 += TT) {
 #pragma unroll
-            for (int k = 0; k < TT; ++k) {
-                const int i = i0 + k;
-                if (i < NFR) {
-                    float2 v[4];
-                    load4<IN>(d, s0 + i, P, p0, v);
+                for (int k = 0; k < TT; ++k) {
+                    const int i = i0 + k;
+                    if (i < NFR) {
+                        const uint32_t slot = pc % R2_NSLOT;
+                        if (!__all_sync(0xffffffffu, mbar_wait32(full0 + 8 * slot, (pc / R2_NSLOT) & 1, wns))) {
+                            ok = false;
+                            break;
+                        }
+                        const uint8_t *fr = r2_smem + slot * C::FB;
+                        float2 v[4];
+                        if constexpr (IN == PFB_IN_C64) {
+                            const float4 a0 = reinterpret_cast<const float4 *>(fr)[2 * t];
+                            const float4 a1 = reinterpret_cast<const float4 *>(fr)[2 * t + 1];
+                            v[0] = make_float2(a0.x, a0.y);
+                            v[1] = make_float2(a0.z, a0.w);
+                            v[2] = make_float2(a1.x, a1.y);
+                            v[3] = make_float2(a1.z, a1.w);
+                        } else if constexpr (IN == PFB_IN_R32) {
+                            const float4 a0 = reinterpret_cast<const float4 *>(fr)[t];
+                            v[0] = make_float2(a0.x, 0.f);
+                            v[1] = make_float2(a0.y, 0.f);
+                            v[2] = make_float2(a0.z, 0.f);
+                            v[3] = make_float2(a0.w, 0.f);
+                        } else {
+                            const int2 a0 = reinterpret_cast<const int2 *>(fr)[t];
+                            const char4 lo = *reinterpret_cast<const char4 *>(&a0.x);
+                            const char4 hi = *reinterpret_cast<const char4 *>(&a0.y);
+                            v[0] = make_float2((float)lo.x * sc, (float)lo.y * sc);
+                            v[1] = make_float2((float)lo.z * sc, (float)lo.w * sc);
+                            v[2] = make_float2((float)hi.x * sc, (float)hi.y * sc);
+                            v[3] = make_float2((float)hi.z * sc, (float)hi.w * sc);
+                        }
+                        // the previous frame's slot goes back: every lane has used its values
+                        __syncwarp();
+                        if (lane == 0 && pc > 0) mbar_arrive(empty0 + 8 * ((pc - 1) % R2_NSLOT));
+                        ++pc;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
+                        for (int j = 0; j < 4; ++j) pend[k][j] = make_float2(h[0][j] * v[j].x, h[0][j] * v[j].y);
 #pragma unroll
-                    for (int m = 1; m < TT; ++m) {
-                        const int js = ((k - m) % TT + TT) % TT;
+                        for (int m = 1; m < TT; ++m) {
+                            const int js = ((k - m) % TT + TT) % TT;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
-                    }
-                    const int r = i - (TT - 1);  // row of the tile completed by this frame
-                    if (r >= 0) {
-                        const int js = (k + 1) % TT;
-                        uint4 hv, lv;
-                        split_bf16x2(pend[js][0], hv.x, lv.x);
-                        split_bf16x2(pend[js][1], hv.y, lv.y);
-                        split_bf16x2(pend[js][2], hv.z, lv.z);
-                        split_bf16x2(pend[js][3], hv.w, lv.w);
-                        const int64_t off = cbase + (r >> 3) * 512 + (r & 7) * 8;  // core matrix (r/8, kg), row r%8
-                        *reinterpret_cast<uint4 *>(yhi + off) = hv;
-                        *reinterpret_cast<uint4 *>(ylo + off) = lv;
+                            for (int j = 0; j < 4; ++j) pend[js][j] = fma2(make_float2(h[m][j], h[m][j]), v[j], pend[js][j]);
+                        }
+                        const int r = i - (TT - 1);
+                        if (r >= 0) {
+                            const int js = (k + 1) % TT;
+                            uint4 hv, lv;
+                            split_bf16x2(pend[js][0], hv.x, lv.x);
+                            split_bf16x2(pend[js][1], hv.y, lv.y);
+                            split_bf16x2(pend[js][2], hv.z, lv.z);
+                            split_bf16x2(pend[js][3], hv.w, lv.w);
+                            const int64_t off = cbase + (r >> 3) * 512 + (r & 7) * 8;
+                            *reinterpret_cast<uint4 *>(yhi + off) = hv;
+                            *reinterpret_cast<uint4 *>(ylo + off) = lv;
+                        }
                     }
                 }
             }
         }
+        if (!ok) *abort_flag = 1;
+    } else {
+        // ---------------- producer warpgroup ----------------
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
+        const int pt = threadIdx.x - F2_THREADS;
+        uint32_t pc = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < ntiles * nchunk && ok; w += gridDim.x) {
+            const int64_t gmt = w / nchunk;
+            const int chunk = (int)(w % nchunk);
+            const int si = find_stream(a, gmt * NTL);
+            const StreamDesc &d = a.s[si];
+            const int64_t s0 = (gmt - d.unit0 / NTL) * Y2_M;
+            for (int i = 0; i < NFR; ++i, ++pc) {
+                const uint32_t slot = pc % R2_NSLOT;
+                if (pc >= R2_NSLOT && !mbar_wait32(empty0 + 8 * slot, ((pc / R2_NSLOT) + 1) & 1, wns)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t dst = smem_u32(r2_smem + slot * C::FB);
+                const int64_t f = s0 + i;
+                if (f < d.n_frames) {
+                    int64_t smp;
+                    const uint8_t *src = static_cast<const uint8_t *>(frame_source(d, f, P, smp)) +
+                                         (smp + (int64_t)chunk * F2_THREADS * F2_BR) * C::ESZ;
+#pragma unroll
+                    for (int q = 0; q < C::NCP; ++q) cp_async16(dst + (pt + 128 * q) * 16, src + (pt + 128 * q) * 16);
+                    cp_async_arrive_noinc(full0 + 8 * slot);
+                } else {
+                    // past the end of the stream: zero frames (rows that are computed, never stored)
+#pragma unroll
+                    for (int q = 0; q < C::NCP; ++q)
+                        *reinterpret_cast<uint4 *>(r2_smem + slot * C::FB + (pt + 128 * q) * 16) = make_uint4(0, 0, 0, 0);
+                    mbar_arrive(full0 + 8 * slot);
+                }
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (!ok) *abort_flag = 1;
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) report_error(a.err, KERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,11 +415,18 @@ static pfb_status launch_fir_tiles(const Plan &plan, const LaunchArgs &a, int64_
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t grid = work < 4 * (int64_t)sms ? work : 4 * (int64_t)sms;
-    k_fir_tiles<IN, TT><<<(unsigned)grid, F2_THREADS, 0, stream>>>(a, plan.P, ntm, yhi, ylo);
+    using C = R2Cfg<IN>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_fir_tiles_ring<IN, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fir_tiles_ring)");
+        attr = true;
+    }
+    const int64_t grid = work < (int64_t)sms ? work : (int64_t)sms;  // one CTA per SM (registers)
+    k_fir_tiles_ring<IN, TT><<<(unsigned)grid, R2_THREADS, C::SMEM, stream>>>(a, plan.P, ntm, yhi, ylo);
     g_launches++;
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? PFB_OK : cuda_fail(e, "launch k_fir_tiles");
+    return e == cudaSuccess ? PFB_OK : cuda_fail(e, "launch k_fir_tiles_ring");
 }
 
 template <int IN>
