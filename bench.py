@@ -9,8 +9,11 @@ FIR + DFT over all 64 streams (load, polyphase FIR, DFT, store).
 
 Printed as one JSON line (rank 0).  Besides the headline value it reports:
   roofline          dominant kernel vs the measured HBM copy bandwidth
-  e2e               same metric through pfb_execute_batch_host (host buffers,
-                    H2D + kernels + D2H inside every step)
+  e2e               same metric through pfb_execute_batch_host (pinned host
+                    buffers: every step moves the input from and the spectra
+                    to host memory; mapped route -- the kernel reads and writes
+                    host memory over the CPU-GPU link -- with the staged route,
+                    H2D + kernels + D2H copies, beside it)
   paths             GSample/s and sampled rel. L2 error vs the FP64 oracle of
                     the DFT routes on the same workload: FP32 FFT, factored
                     split-bf16 tensor-core DFT, dense split-bf16 DFT-matrix
@@ -158,6 +161,40 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+def host_link_peak(nbytes=512 << 20, reps=3):
+    """Concurrent H2D + D2H copy-engine copies of nbytes each way between
+    pinned host and device buffers: bytes moved in both directions per second
+    (GB/s), the ceiling of a step whose input comes from and whose output goes
+    to host memory."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_b = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one():
+        s2.wait_stream(s1)
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+        s1.wait_stream(s2)
+
+    torch.cuda.synchronize()
+    one()
+    torch.cuda.synchronize()
+    e0.record(s1)
+    for _ in range(reps):
+        one()
+    e1.record(s1)
+    torch.cuda.synchronize()
+    gbs = 2 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del h_in, h_out, d_a, d_b
+    return gbs
+
+
 def gpu_index_for(local_rank: int) -> int:
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -952,13 +989,37 @@ def main():
             for _ in range(k2):
                 pkg.pfb_execute_batch_host(host_entries)
             dt = (time.perf_counter() - t0) / k2
+            route = pkg.last_host_route()
+            same = all(np.array_equal(ho.numpy(), o.cpu().numpy()) for ho, o in zip(hout[:4], outs[:4]))
+            # the staged route on the same buffers, for context
+            pkg.set_host_route(pkg.PFB_HOST_ROUTE_STAGED)
+            try:
+                pkg.pfb_execute_batch_host(host_entries)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(k2):
+                    pkg.pfb_execute_batch_host(host_entries)
+                dt_staged = (time.perf_counter() - t0) / k2
+                same_staged = all(np.array_equal(ho.numpy(), o.cpu().numpy()) for ho, o in zip(hout[:4], outs[:4]))
+            finally:
+                pkg.set_host_route(pkg.PFB_HOST_ROUTE_AUTO)
+            link = host_link_peak()
             if local:
                 os.sched_setaffinity(0, old_aff)
-            same = all(np.array_equal(ho.numpy(), o.cpu().numpy()) for ho, o in zip(hout[:4], outs[:4]))
+            moved = n * 8 + len(xs_host) * S * P * 8
             line["e2e"] = {"value": n / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * 8,
                            "d2h_bytes_per_step": len(xs_host) * S * P * 8, "ms_per_step": dt * 1e3,
                            "api": "pfb_execute_batch_host (pinned host buffers, all 64 streams per call)",
+                           "route": route + (" (the kernel reads the input and writes the spectra in host memory "
+                                             "over the CPU-GPU link)" if route == "mapped" else ""),
                            "equal_to_device_path": same,
+                           "staged_route": {"value": n / dt_staged / 1e9, "ms_per_step": dt_staged * 1e3,
+                                            "equal_to_device_path": same_staged},
+                           "host_link": {"bound": "host link", "achieved": moved / dt / 1e9,
+                                         "peak": link, "unit": "GB/s", "frac": moved / dt / 1e9 / link,
+                                         "peak_kind": "concurrent H2D + D2H copy-engine copies of 512 MB each "
+                                                      "way between pinned and device buffers, measured in this run",
+                                         "achieved_kind": "input + spectra bytes per step / e2e step time"},
                            "host_buffers": f"pinned, first touched on the GPU-local CPUs ({len(local)} cpus)"
                            if local else "pinned"}
             del hin, hout, host_entries

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define PFB_API_VERSION 3
+#define PFB_API_VERSION 4
 
 #if defined(__GNUC__)
 #define PFB_API __attribute__((visibility("default")))
@@ -251,19 +251,40 @@ typedef struct pfb_batch_item {
 PFB_API pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_items, void *cuda_stream);
 
 /* pfb_execute_batch from and to HOST memory: items[i].d_in and d_out are
- * host pointers here (pinned memory copies fastest).  The streams are staged
- * through device buffers the library owns (per device, grown with cudaMalloc
- * and kept), in chunks of consecutive items of about 32 MB of input: chunk
- * c's copy-in, kernels and copy-out run on a copy-in stream, cuda_stream and
- * a copy-out stream, three chunks in flight, so copies in both directions
- * overlap the kernels.  Starts after the work already queued on cuda_stream
- * and returns once every output is in host memory.  Results equal those of
- * pfb_execute_batch (and of pfb_execute per stream) bit for bit.  Calls on one
- * device are serialised.  Oversampled plans return PFB_ERR_UNSUPPORTED.
- * Errors: as pfb_execute_batch; PFB_ERR_OOM for the staging buffers;
- * PFB_ERR_TIMEOUT if a device-side wait of a kernel ran out (every plan's
- * error word is read and cleared). */
+ * host pointers here.  Two routes:
+ *  - mapped (taken under PFB_HOST_ROUTE_AUTO when every buffer of the batch
+ *    is page-locked host memory mapped into the device's address space --
+ *    cudaHostAlloc, cudaMallocHost or cudaHostRegister under unified
+ *    addressing -- with both ends of each range mapped and 16-byte aligned,
+ *    and every plan's kernel reads and writes the caller's buffers per thread;
+ *    in this build that is the four-step cluster kernel, variant 3 of the
+ *    FFT path at P = 4096): the kernels read the input and write the spectra
+ *    in host memory over the CPU-GPU link, one launch per variant group on
+ *    cuda_stream, no staging copies;
+ *  - staged (every other case): the streams are staged through device
+ *    buffers the library owns (per device, grown with cudaMalloc and kept),
+ *    in chunks of consecutive items of about 32 MB of input: chunk c's
+ *    copy-in, kernels and copy-out run on a copy-in stream, cuda_stream and a
+ *    copy-out stream, three chunks in flight, so copies in both directions
+ *    overlap the kernels; calls on one device are serialised.
+ * Either route starts after the work already queued on cuda_stream and
+ * returns once every output is in host memory (cuda_stream drained).
+ * Results equal those of pfb_execute_batch (and of pfb_execute per stream)
+ * bit for bit on both routes.  Oversampled plans return
+ * PFB_ERR_UNSUPPORTED.  Errors: as pfb_execute_batch; PFB_ERR_OOM for the
+ * staging buffers; PFB_ERR_TIMEOUT if a device-side wait of a kernel ran out
+ * (every plan's error word is read and cleared). */
 PFB_API pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_t n_items, void *cuda_stream);
+
+/* Route selection of pfb_execute_batch_host, process-wide (default AUTO). */
+#define PFB_HOST_ROUTE_AUTO 0   /* mapped when the batch allows it, else staged */
+#define PFB_HOST_ROUTE_STAGED 1 /* always staged */
+/* Errors: PFB_ERR_INVALID for another value (the route is unchanged). */
+PFB_API pfb_status pfb_set_host_route(int32_t route);
+
+/* The route the calling thread's last pfb_execute_batch_host took: 1 staged,
+ * 2 mapped, 0 if it launched nothing (an invalid batch, or no spectra). */
+PFB_API int32_t pfb_last_host_route(void);
 
 /* A reusable batch: the launches of pfb_execute_batch captured once into a
  * CUDA graph (tile shapes from the autotuner cache), replayed by

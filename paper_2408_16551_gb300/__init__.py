@@ -30,6 +30,8 @@ PFB_IN_R32, PFB_IN_C64, PFB_IN_CI8 = 0, 1, 2
 PFB_WIN_HANN, PFB_WIN_HAMMING, PFB_WIN_BLACKMAN, PFB_WIN_USER = 0, 1, 2, 3
 PFB_DFT_FFT_F32, PFB_DFT_GEMM_F32, PFB_DFT_GEMM_BF16X3 = 0, 1, 2
 PFB_TAPS_CORRELATION, PFB_TAPS_CONVOLUTION = 0, 1
+PFB_HOST_ROUTE_AUTO, PFB_HOST_ROUTE_STAGED = 0, 1
+HOST_ROUTE_NAMES = {0: "none", 1: "staged", 2: "mapped"}  # pfb_last_host_route
 NOALLOC_SCRATCH_BYTES = 32 << 20  # PFB_NOALLOC_SCRATCH_BYTES
 
 EXPORTED = [
@@ -41,7 +43,8 @@ EXPORTED = [
     "pfb_plan_num_variants", "pfb_plan_variant", "pfb_plan_set_variant", "pfb_plan_autotune",
     "pfb_execute_host_noalloc", "pfb_stream_state_size", "pfb_stream_state_export", "pfb_stream_state_import",
     "pfb_synth_out_samples", "pfb_synthesize", "pfb_plan_status", "pfb_plan_set_fault",
-    "pfb_execute_batch_host", "pfb_submit_chunks", "pfb_ticket_times",
+    "pfb_execute_batch_host", "pfb_submit_chunks", "pfb_ticket_times", "pfb_set_host_route",
+    "pfb_last_host_route",
 ]
 
 
@@ -113,6 +116,8 @@ def lib() -> ctypes.CDLL:
             "pfb_stream_state_import": (st, [vp, i64, vp, i64]),
             "pfb_execute_batch": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
             "pfb_execute_batch_host": (st, [ctypes.POINTER(pfb_batch_item), i32, vp]),
+            "pfb_set_host_route": (st, [i32]),
+            "pfb_last_host_route": (i32, []),
             "pfb_batch_create": (st, [ctypes.POINTER(pfb_batch_item), i32, ctypes.POINTER(vp)]),
             "pfb_batch_launch": (st, [vp, vp]),
             "pfb_batch_destroy": (st, [vp]),
@@ -334,8 +339,9 @@ def pfb_execute_batch(entries, stream=None):
 
 def pfb_execute_batch_host(entries, stream=None):
     """entries: list of (Plan, host input ndarray, host output ndarray [>=S, P]
-    complex64); pfb_execute_batch_host stages them through the device and
-    returns once every output is written."""
+    complex64); pfb_execute_batch_host runs them in place (page-locked
+    buffers and a kernel that reads them per thread) or stages them through
+    the device, and returns once every output is written."""
     arr = (pfb_batch_item * max(1, len(entries)))()
     for i, (plan, x, out) in enumerate(entries):
         n = x.size // 2 if plan.in_dtype == PFB_IN_CI8 else x.size
@@ -345,6 +351,16 @@ def pfb_execute_batch_host(entries, stream=None):
         arr[i].d_out = out.ctypes.data if out is not None and out.size else None
         arr[i].out_cap_spectra = (out.size // plan.P) if out is not None else 0
     _check(lib().pfb_execute_batch_host(arr, len(entries), _stream_handle(stream)), "pfb_execute_batch_host")
+
+
+def set_host_route(route: int) -> None:
+    """pfb_set_host_route: PFB_HOST_ROUTE_AUTO (mapped when possible) or PFB_HOST_ROUTE_STAGED."""
+    _check(lib().pfb_set_host_route(route), "pfb_set_host_route")
+
+
+def last_host_route() -> str:
+    """The route this thread's last pfb_execute_batch_host took: "staged", "mapped" or "none"."""
+    return HOST_ROUTE_NAMES.get(int(lib().pfb_last_host_route()), "none")
 
 
 class Batch:

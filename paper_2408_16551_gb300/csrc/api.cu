@@ -1,6 +1,7 @@
 // Host side of the C ABI: status strings, error messages, pfb_execute,
 // pfb_execute_host and the batched entry points (work grouping, CUDA graphs).
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 #include <cstring>
@@ -446,7 +447,50 @@ static pfb_status grow(void **p, size_t *cap, size_t need) {
     return PFB_OK;
 }
 
+// Route of pfb_execute_batch_host (PFB_HOST_ROUTE_*), and the route the
+// calling thread's last call took (0 none, 1 staged, 2 mapped).
+static std::atomic<int> g_host_route{PFB_HOST_ROUTE_AUTO};
+static thread_local int t_last_host_route = 0;
+
+// True when the kernel the plan launches touches the caller's input and
+// spectra only with per-thread accesses (16-byte cp.async reads, plain
+// stores): the four-step cluster kernel.  Kernels that move the caller's
+// buffers with bulk copies, or read each input frame more than once from
+// memory, stay on the staged route.
+static bool reads_buffers_per_thread(const Plan &p) { return p.family == FAM_FFT_CLUSTER && p.variant == 3 && p.R == 1; }
+
+// The device address of the host range [ptr, ptr + bytes) when both its ends
+// are page-locked host memory mapped into the current device's address
+// space (cudaHostAlloc, cudaMallocHost, cudaHostRegister under unified
+// addressing), else nullptr.  Pageable memory gives nullptr.
+static const char *mapped_host_range(const void *ptr, size_t bytes) {
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *dev = static_cast<const char *>(a.devicePointer);
+    if (bytes > 1) {
+        if (cudaPointerGetAttributes(&b, static_cast<const char *>(ptr) + bytes - 1) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (b.type != cudaMemoryTypeHost || static_cast<const char *>(b.devicePointer) != dev + bytes - 1) return nullptr;
+    }
+    return dev;
+}
+
 }  // namespace pfb
+
+extern "C" pfb_status pfb_set_host_route(int32_t route) {
+    clear_error();
+    if (route != PFB_HOST_ROUTE_AUTO && route != PFB_HOST_ROUTE_STAGED) return fail(PFB_ERR_INVALID, "unknown host route");
+    g_host_route.store(route);
+    return PFB_OK;
+}
+
+extern "C" int32_t pfb_last_host_route(void) { return t_last_host_route; }
 
 extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_t n_items, void *cuda_stream) {
     clear_error();
@@ -469,8 +513,55 @@ extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_
         if (it.out_cap_spectra < S[i])
             return fail(PFB_ERR_INVALID, "item " + std::to_string(i) + ": out_cap_spectra smaller than the spectra produced");
     }
+    t_last_host_route = 0;
     if (device < 0) return PFB_OK;
     if (device >= kHostCtxDevices) return fail(PFB_ERR_INVALID, "device ordinal out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // Mapped route: every buffer page-locked and mapped, every plan's kernel
+    // reading and writing them per thread.  The kernels then read the input
+    // and write the spectra in host memory directly (one launch per variant
+    // group, no staging copies), and the call returns after the stream has
+    // drained.
+    if (g_host_route.load() == PFB_HOST_ROUTE_AUTO) {
+        DeviceGuard g(device);
+        std::vector<pfb_batch_item> mapped;
+        bool ok = true;
+        for (int i = 0; i < n_items && ok; ++i) {
+            if (S[i] == 0) continue;
+            const Plan &p = *reinterpret_cast<Plan *>(items[i].plan);
+            const char *di = reads_buffers_per_thread(p) ? mapped_host_range(items[i].d_in, (size_t)fr_bytes[i]) : nullptr;
+            const char *dq = di ? mapped_host_range(items[i].d_out, (size_t)S[i] * p.P * sizeof(float2)) : nullptr;
+            ok = di && dq && aligned16(di) && aligned16(dq);
+            if (!ok) break;
+            pfb_batch_item d = items[i];
+            d.d_in = di;
+            d.n_samples = fr_bytes[i] / p.esize;
+            d.d_out = const_cast<char *>(dq);
+            d.out_cap_spectra = S[i];
+            mapped.push_back(d);
+        }
+        if (ok && !mapped.empty()) {
+            t_last_host_route = 2;
+            std::vector<Group> groups;
+            int dev2 = -1;
+            pfb_status st = build_groups(mapped.data(), (int32_t)mapped.size(), groups, dev2);
+            for (auto &gr : groups) {
+                if (st != PFB_OK) break;
+                st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), s);
+            }
+            // nothing may still be writing host memory when the call returns
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (st != PFB_OK) return st;
+            if (e != cudaSuccess) return cuda_fail(e, "host batch kernels (mapped)");
+            pfb_status kst = PFB_OK;
+            for (int i = 0; i < n_items; ++i) {
+                pfb_status k = take_kernel_error(reinterpret_cast<Plan *>(items[i].plan)->h_err, "pfb_execute_batch_host");
+                if (kst == PFB_OK) kst = k;
+            }
+            return kst;
+        }
+    }
+    t_last_host_route = 1;
     // chunks: runs of consecutive items of about kChunkBytes of input
     constexpr int64_t kChunkBytes = 32ll << 20;
     struct Chunk { int i0, i1; size_t in_bytes, out_bytes; };
@@ -496,7 +587,6 @@ extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_
     HostBatchCtx &x = g_host_ctx[device];
     std::lock_guard<std::mutex> lk(x.mu);
     DeviceGuard g(device);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (!x.ready) {
         PFB_CUDA_TRY(cudaStreamCreateWithFlags(&x.s_in, cudaStreamNonBlocking));
         PFB_CUDA_TRY(cudaStreamCreateWithFlags(&x.s_out, cudaStreamNonBlocking));
