@@ -213,69 +213,90 @@ __global__ void __launch_bounds__(R2_THREADS, 1)
 // ---------------------------------------------------------------------------
 // Pass 2: the product
 // ---------------------------------------------------------------------------
-constexpr int G2_N = 128;                              // reals per N tile (64 bins)
-constexpr int G2_NST = 3;                              // ring stages
-constexpr int G2_CHUNK = 8;                            // K blocks per TMEM accumulation chunk
-constexpr int G2_OPB = Y2_CHUNK_ELEMS * 2;             // bytes of one operand chunk (A: 128 x 64, B: 128 x 64)
-constexpr int G2_STAGE = 4 * G2_OPB;                   // A hi, A lo, B hi, B lo
-constexpr int G2_EPIW = 4, G2_PRODW = 4, G2_MMAW = 5, G2_THREADS = 6 * 32;
-constexpr int G2_SMEM = G2_NST * G2_STAGE + 256 + 1024;  // + barriers, + alignment slack
-constexpr uint32_t G2_TMEM_COLS = 256;                 // two 128-column accumulators
-constexpr uint32_t G2_IDESC = tc_idesc_bf16(128, G2_N);
-constexpr int G2_MB = 8, G2_NB = 16;                   // tile blocks kept together (L2)
+// The MMAs read both operands from shared memory, into which the bulk copies
+// also write: per K block of 64 reals and M = 128 the shared-memory traffic is
+// the stage's bytes written plus 4 K steps x 3 products x (A + B tile) read.
+// At N = 128 that is 64 KB + 96 KB against 12 MMAs of 64 cycles each at the
+// tensor core's rate, which caps the tensor pipe near 60 % at 128 bytes per
+// cycle; at N = 256 it is 96 KB + 144 KB against 12 MMAs of 128 cycles,
+// about 80 %.  So an N tile is 256 reals (128 bins): the full width of one
+// tile of the variant-0 table, in two stages of 96 KB.
+template <int BN>
+struct G2Cfg {
+    static constexpr int N = BN;                             // reals per N tile
+    static constexpr int NST = BN == 256 ? 2 : 3;            // ring stages
+    static constexpr int OPA = Y2_CHUNK_ELEMS * 2;           // bytes of one A chunk (128 x 64 bf16)
+    static constexpr int OPB = BN * Y2_KB * 2;               // bytes of one B chunk (BN x 64 bf16)
+    static constexpr int STAGE = 2 * OPA + 2 * OPB;          // A hi, A lo, B hi, B lo
+    static constexpr int EPIW = BN / 32;                     // epilogue warps: 4 TMEM lane quarters x BN / 128 column halves
+    static constexpr int PRODW = EPIW, MMAW = EPIW + 1, THREADS = (EPIW + 2) * 32;
+    static constexpr int SMEM = NST * STAGE + 256 + 1024;    // + barriers, + alignment slack
+    static constexpr uint32_t TMEM_COLS = 2 * BN;            // two accumulators
+    static constexpr uint32_t IDESC = tc_idesc_bf16(128, BN);
+    static constexpr int MB = 8, NB = 2048 / BN;             // tile blocks kept together (L2): 8 M tiles x 2048 reals
+    static_assert(SMEM <= 232448, "shared memory");
+    static_assert(STAGE < (1 << 20), "transaction count of one stage");
+};
+constexpr int G2_BN = 256;
+constexpr int G2_CHUNK = 8;                                  // K blocks per TMEM accumulation chunk
 
 // tile w of the blocked order -> (global M tile, N tile)
+template <int BN>
 __device__ __forceinline__ void g2_tile(int64_t w, int64_t ntm, int ntn, int64_t &gmt, int &nt) {
-    const int nb = ntn < G2_NB ? ntn : G2_NB;
-    const int64_t bm = w / ((int64_t)G2_MB * ntn);
-    const int64_t idx = w - bm * G2_MB * ntn;
-    const int64_t mrows = min((int64_t)G2_MB, ntm - bm * G2_MB);
+    using C = G2Cfg<BN>;
+    const int nb = ntn < C::NB ? ntn : C::NB;
+    const int64_t bm = w / ((int64_t)C::MB * ntn);
+    const int64_t idx = w - bm * C::MB * ntn;
+    const int64_t mrows = min((int64_t)C::MB, ntm - bm * C::MB);
     const int64_t bn = idx / (mrows * nb), r = idx % (mrows * nb);
-    gmt = bm * G2_MB + r / nb;
+    gmt = bm * C::MB + r / nb;
     nt = (int)(bn * nb + r % nb);
 }
 
-__global__ void __launch_bounds__(G2_THREADS, 1)
+template <int BN>
+__global__ void __launch_bounds__(G2Cfg<BN>::THREADS, 1)
     k_gemm_tiles(const __grid_constant__ LaunchArgs a, int P, int64_t ntm, const __nv_bfloat16 *yhi,
                  const __nv_bfloat16 *ylo) {
+    using C = G2Cfg<BN>;
+    constexpr int NST = C::NST;
     extern __shared__ __align__(1024) uint8_t g2_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(g2_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + G2_NST * G2_STAGE);
-    // full[3], empty[3], dfull[2], dfree[2], then the TMEM address and the abort flag
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[G2_NST]);
-    const uint32_t dfull0 = smem_u32(&bars[2 * G2_NST]), dfree0 = smem_u32(&bars[2 * G2_NST + 2]);
-    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(bars + 2 * G2_NST + 4);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * G2_NST + 5);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NST * C::STAGE);
+    // full[NST], empty[NST], dfull[2], dfree[2], then the TMEM address and the abort flag
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[NST]);
+    const uint32_t dfull0 = smem_u32(&bars[2 * NST]), dfree0 = smem_u32(&bars[2 * NST + 2]);
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(bars + 2 * NST + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * NST + 5);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t wns = a.wait_ns;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < G2_NST; ++i) {
+        for (int i = 0; i < NST; ++i) {
             mbar_init(full0 + 8 * i, 1);   // the producer's arrive.expect_tx + the copies' bytes
             mbar_init(empty0 + 8 * i, 1);  // the MMA thread's commit
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(dfull0 + 8 * i, 1);         // the MMA thread's commit at the end of a chunk
-            mbar_init(dfree0 + 8 * i, G2_EPIW);   // every epilogue warp has read the accumulator
+            mbar_init(dfull0 + 8 * i, 1);        // the MMA thread's commit at the end of a chunk
+            mbar_init(dfree0 + 8 * i, C::EPIW);  // every epilogue warp has read its part of the accumulator
         }
         mbar_init_fence();
         *abort_flag = 0;
     }
-    if (warp == G2_MMAW) tmem_alloc(smem_u32((const void *)tmem_slot), G2_TMEM_COLS);
+    if (warp == C::MMAW) tmem_alloc(smem_u32((const void *)tmem_slot), C::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int ntn = P / 64, KBLK = 2 * P / Y2_KB;
+    const int ntn = 2 * P / BN, KBLK = 2 * P / Y2_KB;
     const int nchunks = (KBLK + G2_CHUNK - 1) / G2_CHUNK;
     const int64_t ntiles = ntm * ntn;
     const __nv_bfloat16 *Bhi = static_cast<const __nv_bfloat16 *>(a.aux);
-    // the variant-0 table: tiles (N tile of 256 reals, K block) of 256 x 64; an N tile
-    // of 128 reals is one contiguous half of one of them
+    // the variant-0 table: tiles (N tile of 256 reals, K block) of 256 x 64, hi then lo; a
+    // 128-real N tile is one contiguous half of one of them
     const __nv_bfloat16 *Blo = Bhi + (int64_t)(P / 128) * KBLK * (2 * Y2_CHUNK_ELEMS);
     const uint32_t sA = smem_u32(sm);
 
-    if (warp == G2_PRODW) {
+    if (warp == C::PRODW) {
         // ---------------- producer: four bulk copies per K block ----------------
         if (lane == 0) {
             uint32_t g = 0;
@@ -283,31 +304,33 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             for (int64_t w = blockIdx.x; w < ntiles && ok; w += gridDim.x) {
                 int64_t gmt;
                 int nt;
-                g2_tile(w, ntm, ntn, gmt, nt);
+                g2_tile<BN>(w, ntm, ntn, gmt, nt);
                 for (int kb = 0; kb < KBLK; ++kb, ++g) {
-                    const uint32_t st = g % G2_NST;
-                    if (g >= G2_NST && !mbar_wait(empty0 + 8 * st, ((g / G2_NST) + 1) & 1, wns)) {
+                    const uint32_t st = g % NST;
+                    if (g >= NST && !mbar_wait(empty0 + 8 * st, ((g / NST) + 1) & 1, wns)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t fb = full0 + 8 * st, dst = sA + st * G2_STAGE;
-                    mbar_expect_tx(fb, G2_STAGE);
+                    const uint32_t fb = full0 + 8 * st, dst = sA + st * C::STAGE;
+                    mbar_expect_tx(fb, C::STAGE);
                     const int64_t ao = (gmt * KBLK + kb) * (int64_t)Y2_CHUNK_ELEMS;
-                    const int64_t bo = ((int64_t)(nt >> 1) * KBLK + kb) * (2 * Y2_CHUNK_ELEMS) + (nt & 1) * Y2_CHUNK_ELEMS;
-                    bulk_g2s(dst, yhi + ao, G2_OPB, fb);
-                    bulk_g2s(dst + G2_OPB, ylo + ao, G2_OPB, fb);
-                    bulk_g2s(dst + 2 * G2_OPB, Bhi + bo, G2_OPB, fb);
-                    bulk_g2s(dst + 3 * G2_OPB, Blo + bo, G2_OPB, fb);
+                    const int64_t bo = BN == 256 ? ((int64_t)nt * KBLK + kb) * (2 * Y2_CHUNK_ELEMS)
+                                                 : ((int64_t)(nt >> 1) * KBLK + kb) * (2 * Y2_CHUNK_ELEMS) +
+                                                       (nt & 1) * Y2_CHUNK_ELEMS;
+                    bulk_g2s(dst, yhi + ao, C::OPA, fb);
+                    bulk_g2s(dst + C::OPA, ylo + ao, C::OPA, fb);
+                    bulk_g2s(dst + 2 * C::OPA, Bhi + bo, C::OPB, fb);
+                    bulk_g2s(dst + 2 * C::OPA + C::OPB, Blo + bo, C::OPB, fb);
                 }
             }
             if (!ok) *abort_flag = 1;
             // every copy issued has landed before the CTA exits
-            const uint32_t first = g > G2_NST ? g - G2_NST : 0;
+            const uint32_t first = g > NST ? g - NST : 0;
             for (uint32_t q = first; q < g; ++q)
-                if (!mbar_wait(full0 + 8 * (q % G2_NST), (q / G2_NST) & 1, wns)) *abort_flag = 1;
+                if (!mbar_wait(full0 + 8 * (q % NST), (q / NST) & 1, wns)) *abort_flag = 1;
         }
         __syncwarp();
-    } else if (warp == G2_MMAW) {
+    } else if (warp == C::MMAW) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             uint32_t g = 0, c = 0;
@@ -319,23 +342,23 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    const uint32_t st = g % G2_NST;
-                    if (!mbar_wait(full0 + 8 * st, (g / G2_NST) & 1, wns)) {
+                    const uint32_t st = g % NST;
+                    if (!mbar_wait(full0 + 8 * st, (g / NST) & 1, wns)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d_t = tmem + buf * G2_N;
-                    const uint32_t ah = sA + st * G2_STAGE, al = ah + G2_OPB, bh = ah + 2 * G2_OPB, bl = ah + 3 * G2_OPB;
+                    const uint32_t d_t = tmem + buf * BN;
+                    const uint32_t ah = sA + st * C::STAGE, al = ah + C::OPA, bh = ah + 2 * C::OPA, bl = bh + C::OPB;
 #pragma unroll
                     for (int ks = 0; ks < Y2_KB / 16; ++ks) {
                         const uint64_t dah = tc_desc_kmajor(ah + ks * 256, 128, 1024);
                         const uint64_t dal = tc_desc_kmajor(al + ks * 256, 128, 1024);
                         const uint64_t dbh = tc_desc_kmajor(bh + ks * 256, 128, 1024);
                         const uint64_t dbl = tc_desc_kmajor(bl + ks * 256, 128, 1024);
-                        tc_mma_ss(d_t, dah, dbh, G2_IDESC, (kb % G2_CHUNK > 0 || ks > 0) ? 1u : 0u);
-                        tc_mma_ss(d_t, dah, dbl, G2_IDESC, 1u);
-                        tc_mma_ss(d_t, dal, dbh, G2_IDESC, 1u);
+                        tc_mma_ss(d_t, dah, dbh, C::IDESC, (kb % G2_CHUNK > 0 || ks > 0) ? 1u : 0u);
+                        tc_mma_ss(d_t, dah, dbl, C::IDESC, 1u);
+                        tc_mma_ss(d_t, dal, dbh, C::IDESC, 1u);
                     }
                     tc_commit(empty0 + 8 * st);  // the stage is free once these MMAs are done
                     issued = true;
@@ -349,22 +372,23 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             // every MMA issued has completed before TMEM is freed
             if (issued && !ok) {
                 const uint32_t gl = g - 1;
-                if (!mbar_wait(empty0 + 8 * (gl % G2_NST), (gl / G2_NST) & 1, wns)) *abort_flag = 1;
+                if (!mbar_wait(empty0 + 8 * (gl % NST), (gl / NST) & 1, wns)) *abort_flag = 1;
             }
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps: TMEM lane quarter = warp ----------------
-        float sacc[G2_N];
+        // ---------------- epilogue warps: TMEM lane quarter warp % 4, columns 128 (warp / 4) .. + 127 ----------------
+        float sacc[128];
         uint32_t c = 0;
         bool ok = true;
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + 128u * half;
         for (int64_t w = blockIdx.x; w < ntiles && ok; w += gridDim.x) {
             int64_t gmt;
             int nt;
-            g2_tile(w, ntm, ntn, gmt, nt);
+            g2_tile<BN>(w, ntm, ntn, gmt, nt);
 #pragma unroll
-            for (int i = 0; i < G2_N; ++i) sacc[i] = 0.f;
+            for (int i = 0; i < 128; ++i) sacc[i] = 0.f;
             for (int cc = 0; cc < nchunks; ++cc, ++c) {
                 const uint32_t buf = c & 1;
                 if (!__all_sync(0xffffffffu, mbar_wait(dfull0 + 8 * buf, (c >> 1) & 1, wns))) {
@@ -373,9 +397,9 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int q = 0; q < G2_N / 32; ++q) {
+                for (int q = 0; q < 4; ++q) {
                     uint32_t r[32];
-                    tmem_ld32(trow + buf * G2_N + 32 * q, r);
+                    tmem_ld32(trow + buf * BN + 32 * q, r);
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) sacc[32 * q + i] += __uint_as_float(r[i]);
@@ -385,13 +409,14 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                 if (lane == 0) mbar_arrive(dfree0 + 8 * buf);
             }
             if (!ok) break;
-            const int si = find_stream(a, gmt * ntn);
+            const int si = find_stream(a, gmt * (P / 64));
             const StreamDesc &d = a.s[si];
-            const int64_t s = (gmt - d.unit0 / ntn) * Y2_M + 32 * warp + lane;
+            const int64_t s = (gmt - d.unit0 / (P / 64)) * Y2_M + 32 * quarter + lane;
             if (s < d.S) {
-                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(d.out) + s * 2 * d.ldo + (int64_t)nt * G2_N);
+                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(d.out) + s * 2 * d.ldo +
+                                                       (int64_t)nt * BN + 128 * half);
 #pragma unroll
-                for (int i = 0; i < G2_N / 4; ++i)
+                for (int i = 0; i < 32; ++i)
                     __stcs(o + i, make_float4(sacc[4 * i], sacc[4 * i + 1], sacc[4 * i + 2], sacc[4 * i + 3]));
             }
         }
@@ -401,7 +426,7 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == G2_MMAW) tmem_dealloc(tmem, G2_TMEM_COLS);
+    if (warp == C::MMAW) tmem_dealloc(tmem, C::TMEM_COLS);
     if (threadIdx.x == 0 && *abort_flag) report_error(a.err, KERR_TIMEOUT);
 }
 
@@ -477,18 +502,19 @@ pfb_status launch_gemm_bf16x3_2p(const Plan &plan, LaunchArgs &a, cudaStream_t s
     default: return fail(PFB_ERR_INVALID, "bad dtype");
     }
     if (st != PFB_OK) return st;
+    using GC = G2Cfg<G2_BN>;
     static int grid_cap = 0;
     if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, G2_SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tiles<G2_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GC::SMEM);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gemm_tiles)");
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid_cap = sms;  // one CTA per SM (198 KB of shared memory)
+        grid_cap = sms;  // one CTA per SM (about 198 KB of shared memory)
     }
-    const int64_t ntiles = ntm * ntn;
+    const int64_t ntiles = ntm * (2 * plan.P / G2_BN);
     const int64_t grid = ntiles < grid_cap ? ntiles : grid_cap;
-    k_gemm_tiles<<<(unsigned)grid, G2_THREADS, G2_SMEM, stream>>>(a, plan.P, ntm, yhi, ylo);
+    k_gemm_tiles<G2_BN><<<(unsigned)grid, GC::THREADS, GC::SMEM, stream>>>(a, plan.P, ntm, yhi, ylo);
     g_launches++;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PFB_OK : cuda_fail(e, "launch k_gemm_tiles");
