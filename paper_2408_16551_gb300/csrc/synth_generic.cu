@@ -5,9 +5,10 @@
 //      into a plan-owned device buffer, either by a radix-2 Stockham FFT in
 //      shared memory with conjugated FP64-built twiddles (FP32 paths) or, for
 //      split-bf16 plans, as the product with the conjugate DFT matrix on the
-//      tensor cores: the dense split-bf16 DFT-matrix kernel of the analysis
-//      run through an internal one-tap plan (taps 1/P, exact in binary) whose
-//      DFT-matrix table is built with the opposite sign;
+//      tensor cores: the dense split-bf16 DFT-matrix product of the analysis
+//      (in two passes for P = 1024, 2048, 4096, else fused) run through an
+//      internal one-tap plan (taps 1/P, exact in binary) whose DFT-matrix
+//      table is built with the opposite sign;
 //   2. the adjoint of the per-branch FIR of Sec. 5.2,
 //        xh[f*P + p] = sum_{m<T, 0 <= f-m < S} h'[m*P + p] y~[f-m, p],
 //      one output sample per thread, coalesced across p.
@@ -124,9 +125,12 @@ static pfb_status ensure_inverse_plan(Plan &p) {
     q->path = PFB_DFT_GEMM_BF16X3;
     q->family = FAM_GEMM_BF16X3;
     q->esize = 8;
-    q->variant = 0;  // the dense DFT-matrix product
     q->hop = p.P;
     q->R = 1;
+    // the dense DFT-matrix product: in two passes (a one-tap FIR pass into the
+    // pre-tiled workspace, then the pipelined GEMM) where that kernel exists,
+    // else fused
+    q->variant = gemm2p_supported(*q) ? 2 : 0;
     q->h_err = p.h_err;  // report into the parent plan's error word
     q->d_err = p.d_err;
     q->wait_ns = p.wait_ns;
@@ -144,6 +148,7 @@ static pfb_status ensure_inverse_plan(Plan &p) {
     if (st != PFB_OK) {
         cudaFree(q->d_taps_pad);
         cudaFree(q->d_dft);
+        cudaFree(q->d_ws2);
         delete q;
         return st;
     }
@@ -155,6 +160,7 @@ void free_inverse_plan(Plan &p) {
     if (!p.inv) return;
     cudaFree(p.inv->d_taps_pad);
     cudaFree(p.inv->d_dft);
+    cudaFree(p.inv->d_ws2);
     delete p.inv;
     p.inv = nullptr;
 }
