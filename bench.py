@@ -547,14 +547,17 @@ def run_oversampled(pkg, device, xs, x_host, spec, reps=50):
     return out
 
 
-def run_synthesis(pkg, device, X_spectra, spec, reps=50):
+def run_synthesis(pkg, device, X_spectra, spec, reps=50, path=None):
     """The synthesis (inverse) filter bank of the c2 analysis output: spectra
-    [16369, 1024] back to (S + T - 1) * P samples; rel. L2 on sampled frames."""
+    [16369, 1024] back to (S + T - 1) * P samples; rel. L2 on sampled frames.
+    path: the plan's DFT path (FP32 FFT by default; split-bf16 runs the inverse
+    DFT as the dense product with the conjugate DFT matrix)."""
     import numpy as np
     import torch
     import oracle
     P, T = spec.P, spec.T
-    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, pkg.PFB_DFT_FFT_F32)
+    path = pkg.PFB_DFT_FFT_F32 if path is None else path
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, spec.window, path)
     S = X_spectra.shape[0]
     n_out = plan.synth_out_samples(S)
     outs = [torch.empty((n_out,), dtype=torch.complex64, device=device) for _ in range(2)]
@@ -580,6 +583,13 @@ def run_synthesis(pkg, device, X_spectra, spec, reps=50):
     out = {"workload": f"synthesis of the c2 analysis output: {S} spectra x P={P} -> {n_out} samples, T={T}",
            "ms": ms, "gsps": n_out / (ms * 1e-3) / 1e9, "rel_l2": oracle.rel_l2(got, ref),
            "hbm_frac": alg / (ms * 1e-3) / (peaks()[0] * 1e9), "kernel": plan.kernel_name}
+    if path == pkg.PFB_DFT_GEMM_BF16X3:
+        # the inverse DFT as the dense product: 24 P executed bf16 flop per spectrum sample
+        fl = S * P * 24.0 * P / (ms * 1e-3) / 1e12
+        out["dtype"] = "bf16x3/f32acc"
+        out["tensor"] = {"executed_tflops": fl, "flop_per_spectrum_sample": 24 * P,
+                         "frac_of_sustained_bf16": fl / peaks()[2],
+                         "note": "the whole call (two-pass product + adjoint FIR) is timed"}
     plan.close()
     return out
 
@@ -1045,6 +1055,8 @@ def main():
             line["c2"] = c2
             line["oversampled"] = run_oversampled(pkg, device, c2_xs, c2_x, c2_spec)
             line["synthesis"] = run_synthesis(pkg, device, c2_last, c2_spec)
+            line["synthesis_bf16x3"] = run_synthesis(pkg, device, c2_last, c2_spec, reps=20,
+                                                     path=pkg.PFB_DFT_GEMM_BF16X3)
             c2_plan.close()
             del c2_xs, c2_last
             torch.cuda.empty_cache()
