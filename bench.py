@@ -195,6 +195,12 @@ def host_link_peak(nbytes=512 << 20, reps=3):
     return gbs
 
 
+def fp32_fma_peak_tflops(sm_mhz: float = 2070.0) -> float:
+    """FP32 FMA rate on the SIMT cores, from unit counts and the maximum SM
+    clock: 152 SMs x 128 lanes x 2 flop per FMA x 2.07 GHz = 80.5 TFLOP/s."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def gpu_index_for(local_rank: int) -> int:
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -436,6 +442,7 @@ def c3_paths(pkg, xs_d, xs_host, specs, stream, reps, names):
                 ent["tensor"] = {"executed_tflops": tfl, "flop_per_sample": fps, "frac_of_sustained_bf16": tfl / bf16s}
             else:
                 ent["fp32_tflops"] = n_total * 8 * P / (ms * 1e-3) / 1e12
+                ent["frac_of_fp32_fma_peak"] = ent["fp32_tflops"] / fp32_fma_peak_tflops()
             out[name] = ent
             if plan.status() != pkg.PFB_OK:
                 out[name]["kernel_status"] = "device-side timeout reported"
@@ -486,6 +493,7 @@ def run_c2(pkg, device, stream, steps, nsets=4, with_e2e=True):
                 ent["tensor"] = {"executed_tflops": tfl, "frac_of_sustained_bf16": tfl / bf16s}
             elif path == pkg.PFB_DFT_GEMM_F32:
                 ent["fp32_tflops"] = n * 8 * P / (ms * 1e-3) / 1e12
+                ent["frac_of_fp32_fma_peak"] = ent["fp32_tflops"] / fp32_fma_peak_tflops()
             res[name] = ent
             if path == pkg.PFB_DFT_FFT_F32:
                 last = outs[(k - 1) % nsets]
