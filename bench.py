@@ -312,10 +312,11 @@ def c3_config(path, P, T, nstreams, n, spectra):
     return {"workload": C3_WORKLOAD + "; one pfb_execute_batch over all streams per step, "
                         + {"fft": "FIR + FFT path (FP32)", "bf16x3": "FIR + factored split-bf16 tensor-core DFT",
                            "bf16x3_dense": "FIR + dense split-bf16 DFT-matrix GEMM",
-                           "bf16x3_dense_2pass": "FIR pass + pipelined dense split-bf16 DFT-matrix GEMM"}[path],
+                           "bf16x3_dense_2pass": "FIR pass + pipelined dense split-bf16 DFT-matrix GEMM",
+                           "f32gemm": "FIR pass + FP32 SIMT DFT-matrix GEMM"}[path],
             "P": P, "T": T, "streams": nstreams, "n_samples": n, "spectra": spectra,
             "path": {"fft": "fft_f32", "bf16x3": "gemm_bf16x3", "bf16x3_dense": "gemm_bf16x3_dense",
-                     "bf16x3_dense_2pass": "gemm_bf16x3_dense_2pass"}[path],
+                     "bf16x3_dense_2pass": "gemm_bf16x3_dense_2pass", "f32gemm": "gemm_f32"}[path],
             "l2": f"inputs larger than L2: each step reads {n * 8 >> 20} MiB and writes "
                   f"{spectra * P * 8 >> 20} MiB (> 129 MB L2); no flush between steps",
             "replicas": "each rank channelises its own copy of the workload (weak scaling, no collective)"}
@@ -827,9 +828,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=20000)
     ap.add_argument("--no-configs", action="store_true", help="skip the c2/c4/oversampled/synthesis lines")
     ap.add_argument("--minimal", action="store_true", help="headline timing only (for profiler runs)")
-    ap.add_argument("--path", default="fft", choices=["fft", "bf16x3", "bf16x3_dense", "bf16x3_dense_2pass"],
+    ap.add_argument("--path", default="fft", choices=["fft", "bf16x3", "bf16x3_dense", "bf16x3_dense_2pass", "f32gemm"],
                     help="DFT route of the headline step (profiler runs): FP32 FFT, factored split-bf16 "
-                         "tensor-core DFT, or the dense split-bf16 DFT-matrix product")
+                         "tensor-core DFT, the dense split-bf16 DFT-matrix product, or the FP32 SIMT one")
     ap.add_argument("--streams", type=int, default=64, help="c3 streams of the headline step (profiler runs)")
     ap.add_argument("--c2-only", action="store_true", help="time only configuration 2 (profiler runs)")
     ap.add_argument("--variant", type=int, default=-1, help="kernel variant of the headline (or --c2-only) plan")
@@ -888,7 +889,7 @@ def main():
     n = n_stream * len(xs_host)
     route = {"fft": (pkg.PFB_DFT_FFT_F32, None), "bf16x3": (pkg.PFB_DFT_GEMM_BF16X3, 1),
              "bf16x3_dense": (pkg.PFB_DFT_GEMM_BF16X3, 0),
-             "bf16x3_dense_2pass": (pkg.PFB_DFT_GEMM_BF16X3, 2)}[args.path]
+             "bf16x3_dense_2pass": (pkg.PFB_DFT_GEMM_BF16X3, 2), "f32gemm": (pkg.PFB_DFT_GEMM_F32, None)}[args.path]
     plan = pkg.Plan(P, T, pkg.PFB_IN_C64, win, route[0])
     if route[1] is not None:
         plan.variant = route[1]
@@ -952,7 +953,7 @@ def main():
         tfl = n * fps / (ms_step_local * 1e-3) / 1e12
         roofline["tensor"] = {"executed_tflops": tfl, "peak_tflops": bf16s, "frac": tfl / bf16s, "flop_per_sample": fps,
                               "peak_source": "sustained bf16 (MEASURED_PEAKS.json)"}
-    dtype = "f32" if route[0] == pkg.PFB_DFT_FFT_F32 else "bf16x3/f32acc"
+    dtype = "bf16x3/f32acc" if route[0] == pkg.PFB_DFT_GEMM_BF16X3 else "f32"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
