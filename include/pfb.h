@@ -288,8 +288,9 @@ PFB_API int32_t pfb_last_host_route(void);
 
 /* A reusable batch: the launches of pfb_execute_batch captured once into a
  * CUDA graph (tile shapes from the autotuner cache), replayed by
- * pfb_batch_launch.  The items' buffers must stay valid while the batch
- * object is used. */
+ * pfb_batch_launch.  The plans' workspaces (the two-pass DFT-matrix
+ * products) are grown before the capture.  The items' buffers and plans must
+ * stay valid while the batch object is used. */
 PFB_API pfb_status pfb_batch_create(const pfb_batch_item *items, int32_t n_items, pfb_batch_t *out_batch);
 PFB_API pfb_status pfb_batch_launch(pfb_batch_t batch, void *cuda_stream);
 PFB_API pfb_status pfb_batch_destroy(pfb_batch_t batch);
@@ -315,8 +316,14 @@ PFB_API int32_t pfb_plan_variant(pfb_plan_t plan);
  * stream), then a pipelined tcgen05 GEMM.  The workspace grows on demand
  * inside pfb_execute / pfb_execute_batch (PFB_ERR_OOM if it cannot), so
  * launches of one plan in that variant must not overlap on different
- * streams, and a CUDA graph of it must be captured after a first launch of
- * the same size. */
+ * streams; pfb_batch_create grows it before capturing, and a graph the caller
+ * captures itself needs an earlier launch of the same size (else
+ * PFB_ERR_UNSUPPORTED).  A buffer the workspace outgrows is kept until the
+ * plan is destroyed, so graphs captured earlier stay valid.  The FP32
+ * DFT-matrix path keeps a workspace by the same rules for P a multiple of
+ * 128 (8 * P bytes per spectrum, rounded up to 128-spectrum blocks per
+ * stream): the FIR pass writes the branch sums there and the GEMM reads
+ * them. */
 PFB_API pfb_status pfb_plan_set_variant(pfb_plan_t plan, int32_t variant);
 /* Time every variant on an input of n_samples (device scratch buffers the
  * call allocates, fills and frees; it synchronises cuda_stream), keep the

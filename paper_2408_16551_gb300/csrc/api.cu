@@ -44,6 +44,12 @@ int64_t family_units(const Plan &plan, int64_t S) {
     }
 }
 
+size_t family_workspace_bytes(const Plan &plan, int64_t nunits) {
+    if (plan.family == FAM_GEMM_F32) return gemm_f32_workspace_bytes(plan, nunits);
+    if (plan.family == FAM_GEMM_BF16X3 && plan.variant == 2) return gemm2p_workspace_bytes(plan, nunits);
+    return 0;
+}
+
 const float *family_taps(const Plan &plan) { return plan.d_taps_pad ? plan.d_taps_pad : plan.d_taps; }
 
 pfb_status alloc_error_words(int n, int **h_err, int **d_err) {
@@ -705,6 +711,18 @@ extern "C" pfb_status pfb_batch_create(const pfb_batch_item *items, int32_t n_it
         cudaGetDevice(&device);
     }
     DeviceGuard g(device);
+    // workspaces of the plans that need one (the two-pass DFT-matrix products)
+    // are grown here, outside the capture, to what each launch will use
+    for (auto &gr : groups) {
+        size_t need = 0;
+        const int nd = (int)gr.descs.size();
+        for (int g0 = 0; g0 < nd; g0 += kMaxStreamsPerLaunch) {
+            int64_t units = 0;
+            for (int i = g0; i < std::min(nd, g0 + kMaxStreamsPerLaunch); ++i) units += family_units(*gr.plan, gr.descs[i].S);
+            need = std::max(need, family_workspace_bytes(*gr.plan, units));
+        }
+        if (need > 0 && (st = grow_plan_workspace(*gr.plan, need, nullptr)) != PFB_OK) return st;
+    }
     Batch *b = new (std::nothrow) Batch();
     if (!b) return fail(PFB_ERR_OOM, "host allocation");
     b->device = device;

@@ -39,6 +39,12 @@ constexpr int F2_THREADS = 256, F2_BR = 4;             // FIR pass: threads, bra
 
 int64_t gemm2p_units(const Plan &plan, int64_t S) { return ((S + Y2_M - 1) / Y2_M) * (plan.P / 64); }
 
+// hi and lo halves: 128-spectrum tiles x (2P / 64) K blocks x 16 KB chunks each
+size_t gemm2p_workspace_bytes(const Plan &plan, int64_t nunits) {
+    const int64_t ntm = nunits / (plan.P / 64);
+    return 2 * (size_t)ntm * (2 * plan.P / Y2_KB) * Y2_CHUNK_ELEMS * sizeof(__nv_bfloat16);
+}
+
 bool gemm2p_supported(const Plan &plan) {
     return (plan.P == 1024 || plan.P == 2048 || plan.P == 4096) && plan.T <= 16 &&
            (plan.TT == 4 || plan.TT == 8 || plan.TT == 16);
@@ -466,32 +472,18 @@ static pfb_status launch_fir_tiles_t(const Plan &plan, const LaunchArgs &a, int6
 
 // The workspace (hi and lo branch sums, 4 x P bytes per padded spectrum) is
 // the plan's and grows on demand: launches of one plan in this variant must
-// not overlap, and the first launch of a size must come before any CUDA-graph
-// capture of it.
+// not overlap, and a CUDA-graph capture needs it grown beforehand (by an
+// earlier launch of the size, or by pfb_batch_create).
 pfb_status launch_gemm_bf16x3_2p(const Plan &plan, LaunchArgs &a, cudaStream_t stream) {
     if (!gemm2p_supported(plan)) return fail(PFB_ERR_UNSUPPORTED, "split-bf16 variant 2 needs P in {1024, 2048, 4096}, T <= 16");
     if (a.nunits <= 0) return PFB_OK;
     if (!plan.d_dft) return fail(PFB_ERR_INTERNAL, "split-bf16 DFT matrix not built");
     const int ntn = plan.P / 64;
     const int64_t ntm = a.nunits / ntn;
-    const size_t half = (size_t)ntm * (2 * plan.P / Y2_KB) * Y2_CHUNK_ELEMS * sizeof(__nv_bfloat16);
+    const size_t half = gemm2p_workspace_bytes(plan, a.nunits) / 2;
+    pfb_status wst = grow_plan_workspace(plan, 2 * half, stream);
+    if (wst != PFB_OK) return wst;
     Plan &mp = const_cast<Plan &>(plan);
-    {
-        std::lock_guard<std::mutex> lk(mp.stage_mu);
-        if (mp.ws2_bytes < 2 * half) {
-            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-            if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
-                return fail(PFB_ERR_UNSUPPORTED, "split-bf16 variant 2: run a launch of this size before capturing it");
-            cudaFree(mp.d_ws2);
-            mp.d_ws2 = nullptr;
-            mp.ws2_bytes = 0;
-            if (cudaMalloc(&mp.d_ws2, 2 * half) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(PFB_ERR_OOM, "split-bf16 variant 2 workspace");
-            }
-            mp.ws2_bytes = 2 * half;
-        }
-    }
     __nv_bfloat16 *yhi = static_cast<__nv_bfloat16 *>(mp.d_ws2);
     __nv_bfloat16 *ylo = yhi + half / sizeof(__nv_bfloat16);
     pfb_status st;

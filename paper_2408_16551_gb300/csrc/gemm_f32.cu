@@ -38,6 +38,11 @@ constexpr int G4_STAGE = G4_BM * G4_ASTR + G4_BK * G4_BN;        // float2 per s
 constexpr int G4_SMEM = G4_NST * G4_STAGE * 8;
 static bool g4_two_pass(const Plan &plan) { return plan.P >= 128 && plan.P % 128 == 0; }
 
+size_t gemm_f32_workspace_bytes(const Plan &plan, int64_t nunits) {
+    if (!g4_two_pass(plan)) return 0;
+    return (size_t)(nunits / (plan.P / G4_BN)) * G4_BM * plan.P * sizeof(float2);
+}
+
 int64_t gemm_f32_units(const Plan &plan, int64_t S) {
     if (g4_two_pass(plan)) return ((S + G4_BM - 1) / G4_BM) * (plan.P / G4_BN);
     return ((S + G3_BM - 1) / G3_BM) * (plan.P / g3_bn(plan.P));
@@ -308,24 +313,9 @@ static pfb_status launch_g4(const Plan &plan, LaunchArgs &a, cudaStream_t stream
     if (a.nunits <= 0) return PFB_OK;
     const int NT = plan.P / G4_BN;
     const int64_t nmb = a.nunits / NT;
-    const size_t bytes = (size_t)nmb * G4_BM * plan.P * sizeof(float2);
+    pfb_status wst = grow_plan_workspace(plan, gemm_f32_workspace_bytes(plan, a.nunits), stream);
+    if (wst != PFB_OK) return wst;
     Plan &mp = const_cast<Plan &>(plan);
-    {
-        std::lock_guard<std::mutex> lk(mp.stage_mu);
-        if (mp.ws2_bytes < bytes) {
-            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-            if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
-                return fail(PFB_ERR_UNSUPPORTED, "FP32 DFT-GEMM: run a launch of this size before capturing it");
-            cudaFree(mp.d_ws2);
-            mp.d_ws2 = nullptr;
-            mp.ws2_bytes = 0;
-            if (cudaMalloc(&mp.d_ws2, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(PFB_ERR_OOM, "FP32 DFT-GEMM workspace");
-            }
-            mp.ws2_bytes = bytes;
-        }
-    }
     float2 *Y = static_cast<float2 *>(mp.d_ws2);
     a.units_per_cta = 0;
     const int64_t fwork = nmb * ((plan.P + G4_FB - 1) / G4_FB);

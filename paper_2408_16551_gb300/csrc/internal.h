@@ -122,9 +122,13 @@ struct Plan {
     // y~ [S][P] and (split-bf16 plans) the internal one-tap inverse plan
     void *d_synth_y = nullptr;
     size_t synth_y_bytes = 0;
-    // split-bf16 variant 2: the pre-tiled hi/lo branch sums (grown on demand by the launch)
+    // the two-pass DFT-matrix products (split-bf16 variant 2, FP32 GEMM for P a
+    // multiple of 128): the branch sums between the passes, grown on demand;
+    // a buffer it outgrows is kept until the plan is destroyed, because a CUDA
+    // graph captured earlier may still use it
     mutable void *d_ws2 = nullptr;
     mutable size_t ws2_bytes = 0;
+    mutable std::vector<void *> ws2_retired;
     Plan *inv = nullptr;
     // host staging for pfb_execute_host
     std::mutex stage_mu;
@@ -168,6 +172,14 @@ void free_error_words(int *h_err);
 pfb_status launch_fft_fast(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_fft_generic(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_f32(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
+size_t gemm_f32_workspace_bytes(const Plan &plan, int64_t nunits);   // 0: no workspace
+size_t gemm2p_workspace_bytes(const Plan &plan, int64_t nunits);
+// bytes of the plan-owned workspace (d_ws2) one launch of nunits work units needs (0: none)
+size_t family_workspace_bytes(const Plan &plan, int64_t nunits);
+// grow the plan's workspace to at least `bytes` (kept; PFB_ERR_OOM if it cannot;
+// PFB_ERR_UNSUPPORTED if it would have to grow while `stream` is capturing)
+pfb_status grow_plan_workspace(const Plan &plan, size_t bytes, cudaStream_t stream);
+void free_plan_workspaces(Plan &plan);
 pfb_status launch_gemm_bf16x3(const Plan &plan, LaunchArgs &args, cudaStream_t stream);
 pfb_status launch_gemm_bf16x3_2p(const Plan &plan, LaunchArgs &args, cudaStream_t stream);  // variant 2
 int64_t gemm2p_units(const Plan &plan, int64_t S);

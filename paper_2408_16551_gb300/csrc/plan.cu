@@ -107,6 +107,33 @@ __global__ void gen_tw_pass_kernel(float2 *tw, int Ns, int R) {
 // ---------------------------------------------------------------------------
 // fast-FFT family twiddles (pass list in fftplan.h)
 // ---------------------------------------------------------------------------
+pfb_status grow_plan_workspace(const Plan &plan, size_t bytes, cudaStream_t stream) {
+    Plan &mp = const_cast<Plan &>(plan);
+    std::lock_guard<std::mutex> lk(mp.stage_mu);
+    if (mp.ws2_bytes >= bytes) return PFB_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (stream && cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(PFB_ERR_UNSUPPORTED, "the plan's workspace would grow inside a stream capture: run a launch "
+                                         "of this size before capturing it");
+    if (mp.d_ws2) mp.ws2_retired.push_back(mp.d_ws2);  // a captured graph may still read it
+    mp.d_ws2 = nullptr;
+    mp.ws2_bytes = 0;
+    if (cudaMalloc(&mp.d_ws2, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PFB_ERR_OOM, "plan workspace");
+    }
+    mp.ws2_bytes = bytes;
+    return PFB_OK;
+}
+
+void free_plan_workspaces(Plan &plan) {
+    cudaFree(plan.d_ws2);
+    plan.d_ws2 = nullptr;
+    plan.ws2_bytes = 0;
+    for (void *q : plan.ws2_retired) cudaFree(q);
+    plan.ws2_retired.clear();
+}
+
 static pfb_status build_pass_table(int P, int MR, float2 **out) {
     const int total = fft_tw_entries(P, MR);
     PFB_CUDA_TRY(cudaMalloc(out, (total > 0 ? total : 1) * sizeof(float2)));
@@ -182,7 +209,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
     cudaFree(p->d_synth_y);
-    cudaFree(p->d_ws2);
+    free_plan_workspaces(*p);
     free_inverse_plan(*p);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;

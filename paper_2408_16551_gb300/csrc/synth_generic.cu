@@ -148,7 +148,7 @@ static pfb_status ensure_inverse_plan(Plan &p) {
     if (st != PFB_OK) {
         cudaFree(q->d_taps_pad);
         cudaFree(q->d_dft);
-        cudaFree(q->d_ws2);
+        free_plan_workspaces(*q);
         delete q;
         return st;
     }
@@ -160,7 +160,7 @@ void free_inverse_plan(Plan &p) {
     if (!p.inv) return;
     cudaFree(p.inv->d_taps_pad);
     cudaFree(p.inv->d_dft);
-    cudaFree(p.inv->d_ws2);
+    free_plan_workspaces(*p.inv);
     delete p.inv;
     p.inv = nullptr;
 }

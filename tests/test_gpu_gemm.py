@@ -347,3 +347,47 @@ def test_gemm_bf16x3_two_pass_unsupported():
     assert plan.num_variants == 3
     with pytest.raises(pkg.PFBError):
         plan.variant = 2
+
+
+@pytest.mark.parametrize("path,P,variant", [(pkg.PFB_DFT_GEMM_F32, 256, None), (pkg.PFB_DFT_GEMM_F32, 1024, None),
+                                            (pkg.PFB_DFT_GEMM_BF16X3, 1024, 2)])
+def test_two_pass_products_in_a_graph_on_fresh_plans(path, P, variant):
+    """The two-pass products keep a plan-owned workspace; pfb_batch_create
+    grows it before capturing, so a graph of fresh plans (never launched)
+    works, and its replays equal per-stream launches bit for bit."""
+    import torch
+    T = 16
+    plan = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HAMMING, path)
+    if variant is not None:
+        plan.variant = variant
+    lens = [P * (T - 1 + 300) + 5, P * (T - 1 + 1), P * 4, P * (T - 1 + 129)]
+    hs = [synth.small_stream(P, T, n, seed=70 + i).generate() for i, n in enumerate(lens)]
+    xs = [to_device(h) for h in hs]
+    outs = [torch.full((max(plan.out_spectra(x.numel()), 1), P), 7.0, dtype=torch.complex64, device="cuda") for x in xs]
+    batch = pkg.Batch([(plan, x, o) for x, o in zip(xs, outs)])
+    for _ in range(2):
+        batch.launch()
+    torch.cuda.synchronize()
+    assert plan.status() == pkg.PFB_OK
+    for x, o in zip(xs, outs):
+        S = plan.out_spectra(x.numel())
+        if S == 0:
+            assert torch.all(o == 7.0)
+            continue
+        assert torch.equal(o[:S], plan.execute(x))
+    tol = (TOL_BF16X3, TOL_MAX_BF16X3) if path == pkg.PFB_DFT_GEMM_BF16X3 else (2e-6, 2e-5)
+    assert_close(outs[0][140:146].cpu().numpy(), reference(hs[0], synth.IN_C64, P, T, synth.WIN_HAMMING, s0=140, ns=6),
+                 *tol, what=f"graph of a fresh plan, path {path}, P={P}")
+    # a larger launch outgrows the workspace; the graph keeps using the buffer it captured
+    big = to_device(synth.small_stream(P, T, P * (T - 1 + 1500), seed=79).generate())
+    plan.execute(big)
+    want = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(7.0)
+    batch.launch()
+    torch.cuda.synchronize()
+    assert plan.status() == pkg.PFB_OK
+    for o, w in zip(outs, want):
+        assert torch.equal(o, w)
+    batch.close()
+    plan.close()
