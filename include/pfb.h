@@ -174,15 +174,22 @@ PFB_API pfb_status pfb_plan_get_taps(pfb_plan_t plan, double *host_out, int64_t 
 PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samples,
                        void *d_out, int64_t out_cap_spectra, void *cuda_stream);
 
-/* Same as pfb_execute, from and to HOST memory: the library stages the input
- * through device buffers it owns and returns after the output is in host_out.
- * The work is pipelined over chunks of about 16 MB of input: host->device
- * copies on an internal stream, kernels on cuda_stream, device->host copies
- * on a second internal stream, so both copy directions and the kernels
- * overlap; it starts after the work already queued on cuda_stream.  Results
- * equal those of pfb_execute.  Pinned host memory gives the fastest copies.
- * Returns PFB_ERR_TIMEOUT (output not valid) if a device-side wait of a
- * kernel ran out; the plan's error word is cleared by the call. */
+/* Same as pfb_execute, from and to HOST memory; returns after the output is
+ * in host_out and starts after the work already queued on cuda_stream.  Two
+ * routes, chosen as in pfb_execute_batch_host (pfb_set_host_route):
+ *  - mapped: both buffers page-locked and mapped into the device's address
+ *    space (both ends of each range), 16-byte aligned, and the plan's kernel
+ *    takes host buffers (the four-step kernel at P = 4096, the
+ *    warp-specialised single-CTA kernel, FFT path variant 5, at P <= 1024):
+ *    the kernel reads the input and writes the spectra in host memory over
+ *    the CPU-GPU link;
+ *  - staged: the library stages the input through device buffers it owns,
+ *    pipelined over chunks of about 16 MB of input: host->device copies on an
+ *    internal stream, kernels on cuda_stream, device->host copies on a second
+ *    internal stream, so both copy directions and the kernels overlap.
+ * Results equal those of pfb_execute on both routes.  Returns
+ * PFB_ERR_TIMEOUT (output not valid) if a device-side wait of a kernel ran
+ * out; the plan's error word is cleared by the call. */
 PFB_API pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples,
                             void *host_out, int64_t out_cap_spectra, void *cuda_stream);
 
@@ -256,11 +263,11 @@ PFB_API pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_item
  *    is page-locked host memory mapped into the device's address space --
  *    cudaHostAlloc, cudaMallocHost or cudaHostRegister under unified
  *    addressing -- with both ends of each range mapped and 16-byte aligned,
- *    and every plan's kernel reads and writes the caller's buffers per thread;
- *    in this build that is the four-step cluster kernel, variant 3 of the
- *    FFT path at P = 4096): the kernels read the input and write the spectra
- *    in host memory over the CPU-GPU link, one launch per variant group on
- *    cuda_stream, no staging copies;
+ *    and every plan's kernel takes host buffers: the four-step cluster
+ *    kernel, variant 3 of the FFT path at P = 4096, and the warp-specialised
+ *    single-CTA kernel, variant 5 at P <= 1024): the kernels read the input
+ *    and write the spectra in host memory over the CPU-GPU link, one launch
+ *    per variant group on cuda_stream, no staging copies;
  *  - staged (every other case): the streams are staged through device
  *    buffers the library owns (per device, grown with cudaMalloc and kept),
  *    in chunks of consecutive items of about 32 MB of input: chunk c's
@@ -282,8 +289,9 @@ PFB_API pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_t n
 /* Errors: PFB_ERR_INVALID for another value (the route is unchanged). */
 PFB_API pfb_status pfb_set_host_route(int32_t route);
 
-/* The route the calling thread's last pfb_execute_batch_host took: 1 staged,
- * 2 mapped, 0 if it launched nothing (an invalid batch, or no spectra). */
+/* The route the calling thread's last pfb_execute_batch_host or
+ * pfb_execute_host took: 1 staged, 2 mapped, 0 if it launched nothing (an
+ * invalid call, or no spectra). */
 PFB_API int32_t pfb_last_host_route(void);
 
 /* A reusable batch: the launches of pfb_execute_batch captured once into a

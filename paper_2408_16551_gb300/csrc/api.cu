@@ -87,7 +87,7 @@ pfb_status take_kernel_error(int *h_err, const char *what) {
 
 // Launch the plan's family kernel over n stream descriptors (all of this
 // family/P/T/dtype), in groups of kMaxStreamsPerLaunch.
-pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err) {
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err, bool mapped) {
     for (int g0 = 0; g0 < n; g0 += kMaxStreamsPerLaunch) {
         const int g1 = std::min(n, g0 + kMaxStreamsPerLaunch);
         LaunchArgs a;
@@ -109,6 +109,7 @@ pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_
         a.err = err ? err : plan.d_err;
         a.wait_ns = plan.wait_ns;
         a.fault = plan.fault;
+        a.mapped = mapped ? 1 : 0;
         pfb_status st;
         switch (plan.family) {
         case FAM_FFT_FAST: st = launch_fft_fast(plan, a, stream); break;
@@ -270,6 +271,52 @@ extern "C" pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_s
     return launch_family(p, d, nd, static_cast<cudaStream_t>(cuda_stream));
 }
 
+namespace pfb {
+
+// Route of the host-buffer calls (PFB_HOST_ROUTE_*), and the route the
+// calling thread's last one took (0 none, 1 staged, 2 mapped).
+static std::atomic<int> g_host_route{PFB_HOST_ROUTE_AUTO};
+static thread_local int t_last_host_route = 0;
+
+// True when the kernel the plan launches can take page-locked host buffers
+// (launch flag `mapped`): every access to the caller's input and spectra is
+// then a per-thread one (16-byte cp.async reads, plain stores).  The
+// four-step cluster kernel always reads that way; the warp-specialised
+// single-CTA kernel (FFT path variant 5) switches its producer from bulk
+// copies to cp.async under the flag.  Kernels that read each input frame
+// more than once from memory, or move the caller's buffers with bulk copies
+// only, stay on the staged route.
+static bool takes_mapped_buffers(const Plan &p) {
+    if (p.R != 1) return false;
+    if (p.family == FAM_FFT_CLUSTER) return p.variant == 3;
+    if (p.family == FAM_FFT_FAST) return p.variant == 5;
+    return false;
+}
+
+// The device address of the host range [ptr, ptr + bytes) when both its ends
+// are page-locked host memory mapped into the current device's address
+// space (cudaHostAlloc, cudaMallocHost, cudaHostRegister under unified
+// addressing), else nullptr.  Pageable memory gives nullptr.
+static const char *mapped_host_range(const void *ptr, size_t bytes) {
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *dev = static_cast<const char *>(a.devicePointer);
+    if (bytes > 1) {
+        if (cudaPointerGetAttributes(&b, static_cast<const char *>(ptr) + bytes - 1) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (b.type != cudaMemoryTypeHost || static_cast<const char *>(b.devicePointer) != dev + bytes - 1) return nullptr;
+    }
+    return dev;
+}
+
+}  // namespace pfb
+
 extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int64_t n_samples, void *host_out,
                                        int64_t out_cap_spectra, void *cuda_stream) {
     clear_error();
@@ -283,6 +330,29 @@ extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int
     if (out_cap_spectra < S) return fail(PFB_ERR_INVALID, "out_cap_spectra smaller than the spectra produced");
     const size_t in_bytes = (size_t)n_samples * p.esize;
     const size_t out_bytes = (size_t)S * p.P * sizeof(float2);
+    t_last_host_route = 0;
+    // Mapped route (as in pfb_execute_batch_host): page-locked, mapped,
+    // 16-byte aligned buffers and a kernel that takes them; it reads the
+    // input and writes the spectra in host memory, then the stream drains.
+    if (g_host_route.load() == PFB_HOST_ROUTE_AUTO && takes_mapped_buffers(p)) {
+        DeviceGuard g(p.device);
+        const int64_t fr = (n_samples / p.P) * p.P;  // whole frames only
+        const char *di = mapped_host_range(host_in, (size_t)fr * p.esize);
+        const char *dq = di ? mapped_host_range(host_out, out_bytes) : nullptr;
+        if (di && dq && aligned16(di) && aligned16(dq)) {
+            t_last_host_route = 2;
+            cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+            StreamDesc d[kMaxStreamsPerLaunch];
+            int nd = 0;
+            pfb_status st = make_stream_descs(p, di, fr, const_cast<char *>(dq), S, d, &nd);
+            if (st == PFB_OK && nd > 0) st = launch_family(p, d, nd, s, nullptr, true);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (st != PFB_OK) return st;
+            if (e != cudaSuccess) return cuda_fail(e, "pfb_execute_host kernels (mapped)");
+            return take_kernel_error(p.h_err, "pfb_execute_host");
+        }
+    }
+    t_last_host_route = 1;
     std::lock_guard<std::mutex> lk(p.stage_mu);
     DeviceGuard g(p.device);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -453,40 +523,6 @@ static pfb_status grow(void **p, size_t *cap, size_t need) {
     return PFB_OK;
 }
 
-// Route of pfb_execute_batch_host (PFB_HOST_ROUTE_*), and the route the
-// calling thread's last call took (0 none, 1 staged, 2 mapped).
-static std::atomic<int> g_host_route{PFB_HOST_ROUTE_AUTO};
-static thread_local int t_last_host_route = 0;
-
-// True when the kernel the plan launches touches the caller's input and
-// spectra only with per-thread accesses (16-byte cp.async reads, plain
-// stores): the four-step cluster kernel.  Kernels that move the caller's
-// buffers with bulk copies, or read each input frame more than once from
-// memory, stay on the staged route.
-static bool reads_buffers_per_thread(const Plan &p) { return p.family == FAM_FFT_CLUSTER && p.variant == 3 && p.R == 1; }
-
-// The device address of the host range [ptr, ptr + bytes) when both its ends
-// are page-locked host memory mapped into the current device's address
-// space (cudaHostAlloc, cudaMallocHost, cudaHostRegister under unified
-// addressing), else nullptr.  Pageable memory gives nullptr.
-static const char *mapped_host_range(const void *ptr, size_t bytes) {
-    cudaPointerAttributes a{}, b{};
-    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-    const char *dev = static_cast<const char *>(a.devicePointer);
-    if (bytes > 1) {
-        if (cudaPointerGetAttributes(&b, static_cast<const char *>(ptr) + bytes - 1) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        if (b.type != cudaMemoryTypeHost || static_cast<const char *>(b.devicePointer) != dev + bytes - 1) return nullptr;
-    }
-    return dev;
-}
-
 }  // namespace pfb
 
 extern "C" pfb_status pfb_set_host_route(int32_t route) {
@@ -535,7 +571,7 @@ extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_
         for (int i = 0; i < n_items && ok; ++i) {
             if (S[i] == 0) continue;
             const Plan &p = *reinterpret_cast<Plan *>(items[i].plan);
-            const char *di = reads_buffers_per_thread(p) ? mapped_host_range(items[i].d_in, (size_t)fr_bytes[i]) : nullptr;
+            const char *di = takes_mapped_buffers(p) ? mapped_host_range(items[i].d_in, (size_t)fr_bytes[i]) : nullptr;
             const char *dq = di ? mapped_host_range(items[i].d_out, (size_t)S[i] * p.P * sizeof(float2)) : nullptr;
             ok = di && dq && aligned16(di) && aligned16(dq);
             if (!ok) break;
@@ -553,7 +589,7 @@ extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_
             pfb_status st = build_groups(mapped.data(), (int32_t)mapped.size(), groups, dev2);
             for (auto &gr : groups) {
                 if (st != PFB_OK) break;
-                st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), s);
+                st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), s, nullptr, true);
             }
             // nothing may still be writing host memory when the call returns
             cudaError_t e = cudaStreamSynchronize(s);
