@@ -516,19 +516,8 @@ def run_c2(pkg, device, stream, steps, nsets=4, with_e2e=True):
         for _ in range(k2):
             fft_plan.execute_host(hin.numpy(), hout.numpy())
         dt = (time.perf_counter() - t0) / k2
-        route = pkg.last_host_route()
-        pkg.set_host_route(pkg.PFB_HOST_ROUTE_STAGED)
-        try:
-            fft_plan.execute_host(hin.numpy(), hout.numpy())
-            t0 = time.perf_counter()
-            for _ in range(k2):
-                fft_plan.execute_host(hin.numpy(), hout.numpy())
-            dt_staged = (time.perf_counter() - t0) / k2
-        finally:
-            pkg.set_host_route(pkg.PFB_HOST_ROUTE_AUTO)
         out["e2e"] = {"value": n / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": S * P * 8,
-                      "api": "pfb_execute_host (pinned host buffers)", "route": route,
-                      "staged_route": {"value": n / dt_staged / 1e9}}
+                      "api": "pfb_execute_host (pinned host buffers)", "route": pkg.last_host_route()}
     return out, fft_plan, xs, last, spec, x
 
 

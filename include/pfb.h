@@ -178,15 +178,15 @@ PFB_API pfb_status pfb_execute(pfb_plan_t plan, const void *d_in, int64_t n_samp
  * in host_out and starts after the work already queued on cuda_stream.  Two
  * routes, chosen as in pfb_execute_batch_host (pfb_set_host_route):
  *  - mapped: both buffers page-locked and mapped into the device's address
- *    space (both ends of each range), 16-byte aligned, and the plan's kernel
- *    takes host buffers (the four-step kernel at P = 4096, the
- *    warp-specialised single-CTA kernel, FFT path variant 5, at P <= 1024):
- *    the kernel reads the input and writes the spectra in host memory over
- *    the CPU-GPU link;
+ *    space (both ends of each range), 16-byte aligned, and the plan on the
+ *    four-step cluster kernel (FFT path, P = 4096, variant 3): the kernel
+ *    reads the input and writes the spectra in host memory over the CPU-GPU
+ *    link;
  *  - staged: the library stages the input through device buffers it owns,
  *    pipelined over chunks of about 16 MB of input: host->device copies on an
  *    internal stream, kernels on cuda_stream, device->host copies on a second
  *    internal stream, so both copy directions and the kernels overlap.
+ *    Pinned host memory gives the fastest copies.
  * Results equal those of pfb_execute on both routes.  Returns
  * PFB_ERR_TIMEOUT (output not valid) if a device-side wait of a kernel ran
  * out; the plan's error word is cleared by the call. */
@@ -263,11 +263,11 @@ PFB_API pfb_status pfb_execute_batch(const pfb_batch_item *items, int32_t n_item
  *    is page-locked host memory mapped into the device's address space --
  *    cudaHostAlloc, cudaMallocHost or cudaHostRegister under unified
  *    addressing -- with both ends of each range mapped and 16-byte aligned,
- *    and every plan's kernel takes host buffers: the four-step cluster
- *    kernel, variant 3 of the FFT path at P = 4096, and the warp-specialised
- *    single-CTA kernel, variant 5 at P <= 1024): the kernels read the input
- *    and write the spectra in host memory over the CPU-GPU link, one launch
- *    per variant group on cuda_stream, no staging copies;
+ *    and every plan's kernel reads and writes the caller's buffers per thread;
+ *    in this build that is the four-step cluster kernel, variant 3 of the
+ *    FFT path at P = 4096): the kernels read the input and write the spectra
+ *    in host memory over the CPU-GPU link, one launch per variant group on
+ *    cuda_stream, no staging copies;
  *  - staged (every other case): the streams are staged through device
  *    buffers the library owns (per device, grown with cudaMalloc and kept),
  *    in chunks of consecutive items of about 32 MB of input: chunk c's

@@ -87,7 +87,7 @@ pfb_status take_kernel_error(int *h_err, const char *what) {
 
 // Launch the plan's family kernel over n stream descriptors (all of this
 // family/P/T/dtype), in groups of kMaxStreamsPerLaunch.
-pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err, bool mapped) {
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err) {
     for (int g0 = 0; g0 < n; g0 += kMaxStreamsPerLaunch) {
         const int g1 = std::min(n, g0 + kMaxStreamsPerLaunch);
         LaunchArgs a;
@@ -109,7 +109,6 @@ pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_
         a.err = err ? err : plan.d_err;
         a.wait_ns = plan.wait_ns;
         a.fault = plan.fault;
-        a.mapped = mapped ? 1 : 0;
         pfb_status st;
         switch (plan.family) {
         case FAM_FFT_FAST: st = launch_fft_fast(plan, a, stream); break;
@@ -278,20 +277,14 @@ namespace pfb {
 static std::atomic<int> g_host_route{PFB_HOST_ROUTE_AUTO};
 static thread_local int t_last_host_route = 0;
 
-// True when the kernel the plan launches can take page-locked host buffers
-// (launch flag `mapped`): every access to the caller's input and spectra is
-// then a per-thread one (16-byte cp.async reads, plain stores).  The
-// four-step cluster kernel always reads that way; the warp-specialised
-// single-CTA kernel (FFT path variant 5) switches its producer from bulk
-// copies to cp.async under the flag.  Kernels that read each input frame
-// more than once from memory, or move the caller's buffers with bulk copies
-// only, stay on the staged route.
-static bool takes_mapped_buffers(const Plan &p) {
-    if (p.R != 1) return false;
-    if (p.family == FAM_FFT_CLUSTER) return p.variant == 3;
-    if (p.family == FAM_FFT_FAST) return p.variant == 5;
-    return false;
-}
+// True when the kernel the plan launches touches the caller's input and
+// spectra only with per-thread accesses (16-byte cp.async reads, plain
+// stores): the four-step cluster kernel.  Kernels that move the caller's
+// buffers with bulk copies, or read each input frame more than once from
+// memory, stay on the staged route.  (A per-thread copy producer for the
+// warp-specialised single-CTA kernel measured 3 % slower than staging on a
+// 2^24-sample stream at P = 1024, so it has none.)
+static bool takes_mapped_buffers(const Plan &p) { return p.family == FAM_FFT_CLUSTER && p.variant == 3 && p.R == 1; }
 
 // The device address of the host range [ptr, ptr + bytes) when both its ends
 // are page-locked host memory mapped into the current device's address
@@ -345,7 +338,7 @@ extern "C" pfb_status pfb_execute_host(pfb_plan_t plan, const void *host_in, int
             StreamDesc d[kMaxStreamsPerLaunch];
             int nd = 0;
             pfb_status st = make_stream_descs(p, di, fr, const_cast<char *>(dq), S, d, &nd);
-            if (st == PFB_OK && nd > 0) st = launch_family(p, d, nd, s, nullptr, true);
+            if (st == PFB_OK && nd > 0) st = launch_family(p, d, nd, s);
             cudaError_t e = cudaStreamSynchronize(s);
             if (st != PFB_OK) return st;
             if (e != cudaSuccess) return cuda_fail(e, "pfb_execute_host kernels (mapped)");
@@ -589,7 +582,7 @@ extern "C" pfb_status pfb_execute_batch_host(const pfb_batch_item *items, int32_
             pfb_status st = build_groups(mapped.data(), (int32_t)mapped.size(), groups, dev2);
             for (auto &gr : groups) {
                 if (st != PFB_OK) break;
-                st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), s, nullptr, true);
+                st = launch_family(*gr.plan, gr.descs.data(), (int)gr.descs.size(), s);
             }
             // nothing may still be writing host memory when the call returns
             cudaError_t e = cudaStreamSynchronize(s);

@@ -59,8 +59,7 @@ struct WsCfg {
     static constexpr int NFFTT = NFFTW * 32;
     static constexpr int PRODW = NFIRW + NFFTW;                      // producer warp index
     // with setmaxnreg the producer sits in a warpgroup of its own (3 idle warps)
-    static constexpr int NPROD = SETMAXNREG ? 128 : 32;              // threads of the producer warp(group)
-    static constexpr int NTHREADS = NFT + NFFTT + NPROD;
+    static constexpr int NTHREADS = NFT + NFFTT + (SETMAXNREG ? 128 : 32);
     static constexpr int SB = 4;                                     // spectra per FFT batch
     static_assert(TT % SB == 0, "batch rows follow the frame loop's unrolling");
     static constexpr int MR = 16;
@@ -475,9 +474,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSLOT; ++i) {
-            // bulk copies: the producer's arrive.expect_tx; mapped host input: one
-            // copy-completion arrival per producer thread
-            mbar_init(full0 + 8 * i, (!TC && a.mapped) ? C::NPROD : 1);
+            mbar_init(full0 + 8 * i, 1);
             mbar_init(empty0 + 8 * i, C::NFIRW);
         }
         for (int i = 0; i < 2; ++i) {
@@ -736,36 +733,7 @@ __global__ void __launch_bounds__(WsCfg<P, TT, IN, TC>::NTHREADS, 1) k_fft_ws(co
                                     smem_u32(&bars[2 * NSLOT + 4]), smem_u32(&bars[2 * NSLOT + 5]), *tmem_slot,
                                     abort_flag);
         }
-        if (!TC && a.mapped) {
-            // page-locked host input (read over the CPU-GPU link): every producer
-            // thread gathers 16-byte pieces of the frame with cp.async, and its
-            // arrival on the slot's full barrier fires once they have landed
-            const int pt = threadIdx.x - C::PRODW * 32;
-            uint32_t pc = 0;
-            bool ok = a.fault != FAULT_NO_COPIES;
-            int si;
-            int64_t sA, sB;
-            while (ok && ws_next_segment(a, range, si, sA, sB)) {
-                const StreamDesc &d = a.s[si];
-                const int64_t f_end = sB + TT - 1;
-                const uint8_t *in = static_cast<const uint8_t *>(d.in);
-                for (int64_t f = sA; f < f_end && ok; ++f, ++pc) {
-                    const uint32_t slot = pc % NSLOT;
-                    if (pc >= NSLOT && !mbar_wait(empty0 + 8 * slot, ((pc / NSLOT) + 1) & 1, a.wait_ns)) {
-                        *abort_flag = 1;
-                        ok = false;
-                        break;
-                    }
-                    const uint8_t *src;
-                    if (f < d.n_state) src = static_cast<const uint8_t *>(d.state) + f * (int64_t)C::FB;
-                    else src = in + (f - d.n_state) * (int64_t)C::FB;
-                    const uint32_t dst = smem_u32(ring + slot * C::FB);
-                    for (int q = pt; q < C::FB / 16; q += C::NPROD) cp_async16(dst + 16 * q, src + 16 * q);
-                    cp_async_arrive_noinc(full0 + 8 * slot);
-                }
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-        } else if (warp == C::PRODW && lane == 0) {
+        if (warp == C::PRODW && lane == 0) {
             uint32_t pc = 0;
             // error-reporting test hook: with FAULT_NO_COPIES the producer
             // issues no copies at all, so every consumer's bounded wait runs

@@ -77,8 +77,7 @@ struct LaunchArgs {
     int *err;               // error word (host-mapped memory): KERR_* of a failed launch
     uint64_t wait_ns;       // bound of the kernel's device-side waits (%globaltimer ns)
     int32_t fault;          // FAULT_* test hook (0 in normal use)
-    int32_t mapped;         // 1: the buffers are page-locked host memory; kernels that
-                            // otherwise move input with bulk copies use per-thread copies
+    int32_t pad_;
 };
 
 // ---------------------------------------------------------------------------
@@ -154,8 +153,7 @@ int ilog2(int64_t v);
 // the plan's P, T, dtype).  `descs` unit0 fields are filled in here.  The
 // kernels report failures into `err` (device address of a host-mapped word;
 // nullptr = the plan's own word).
-pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err = nullptr,
-                         bool mapped = false);
+pfb_status launch_family(const Plan &plan, StreamDesc *descs, int n, cudaStream_t stream, int *err = nullptr);
 
 // Read and clear a host-mapped error word: PFB_OK, or the status a kernel's
 // KERR_* code maps to (KERR_TIMEOUT -> PFB_ERR_TIMEOUT, others ->

@@ -204,10 +204,8 @@ def test_mapped_route_falls_back_to_staged():
         entries2.append((p, vx, vo))
         outs2.append(vo)
     run(entries2, outs2, "mapped")
-    # the same plus a P = 1024 stream on a kernel that moves its input with bulk copies only
-    # (a tile shape of the fused kernel, variant 0)
+    # the same plus a P = 1024 stream (a kernel that moves its input with bulk copies)
     other = pkg.Plan(1024, 16, synth.IN_C64, synth.WIN_BLACKMAN)
-    other.variant = 0
     y = synth.small_stream(1024, 16, 1024 * 40, in_dtype=synth.IN_C64, seed=401).generate()
     by, vy = _pinned_copy(y)
     bq, vq = _pinned_copy(np.empty((other.out_spectra(y.size), 1024), np.complex64))
@@ -221,18 +219,18 @@ def test_mapped_route_falls_back_to_staged():
         p.close()
 
 
-@pytest.mark.parametrize("P,T,dt,variant", [(1024, 16, synth.IN_C64, 5), (512, 8, synth.IN_CI8, 5),
-                                            (256, 16, synth.IN_R32, 5), (4096, 16, synth.IN_C64, 3)])
-def test_execute_host_mapped_route(P, T, dt, variant):
-    """pfb_execute_host with page-locked buffers on a kernel that takes them
-    (the warp-specialised kernel with its per-thread copy producer, the
-    four-step kernel): the mapped route, bitwise equal to the device path and
-    to the staged route; the oracle on sampled rows."""
+@pytest.mark.parametrize("T,dt", [(16, synth.IN_C64), (8, synth.IN_CI8), (4, synth.IN_R32)])
+def test_execute_host_mapped_route(T, dt):
+    """pfb_execute_host with page-locked buffers on the four-step kernel
+    (P = 4096): the mapped route, bitwise equal to the device path and to the
+    staged route; the oracle on sampled rows.  A P = 1024 plan on the same
+    kind of buffers stays staged."""
     import torch
+    P = 4096
     plan = pkg.Plan(P, T, dt, synth.WIN_HAMMING)
-    plan.variant = variant
-    n = P * (T - 1 + 777) + 13
-    x = synth.small_stream(P, T, n, in_dtype=dt, seed=P + T).generate()
+    assert plan.variant == 3
+    n = P * (T - 1 + 333) + 13
+    x = synth.small_stream(P, T, n, in_dtype=dt, seed=T + 900).generate()
     S = plan.out_spectra(_n(plan, x))
     ref = plan.execute(to_device(x)).cpu().numpy()
     torch.cuda.synchronize()
@@ -249,21 +247,14 @@ def test_execute_host_mapped_route(P, T, dt, variant):
         pkg.set_host_route(pkg.PFB_HOST_ROUTE_AUTO)
     rows = [0, S // 2, S - 1]
     want = np.concatenate([reference(x, dt, P, T, synth.WIN_HAMMING, s0=r, ns=1) for r in rows])
-    assert_close(vo[rows], want, TOL_F32, TOL_MAX_F32, what=f"mapped pfb_execute_host P={P}")
-    # a batch of such streams from page-locked buffers takes the mapped route too
-    xs = [synth.small_stream(P, T, P * (T - 1 + k) + 3, in_dtype=dt, seed=P + k).generate() for k in (1, 50, 300)]
-    keep, entries, outs, refs = [], [], [], []
-    for xi in xs:
-        Si = plan.out_spectra(_n(plan, xi))
-        refs.append(plan.execute(to_device(xi)).cpu().numpy())
-        b1, v1 = _pinned_copy(xi)
-        b2, v2 = _pinned_copy(np.zeros((Si, P), np.complex64))
-        keep += [b1, b2]
-        entries.append((plan, v1, v2))
-        outs.append(v2)
-    pkg.pfb_execute_batch_host(entries)
-    assert pkg.last_host_route() == "mapped"
-    for o, r in zip(outs, refs):
-        assert np.array_equal(o, r)
+    assert_close(vo[rows], want, TOL_F32, TOL_MAX_F32, what=f"mapped pfb_execute_host T={T}")
     assert plan.status() == pkg.PFB_OK
     plan.close()
+    small = pkg.Plan(1024, 16, synth.IN_C64, synth.WIN_HAMMING)
+    y = synth.small_stream(1024, 16, 1024 * 60, seed=901).generate()
+    by, vy = _pinned_copy(y)
+    bq, vq = _pinned_copy(np.zeros((small.out_spectra(y.size), 1024), np.complex64))
+    small.execute_host(vy, vq)
+    assert pkg.last_host_route() == "staged"
+    assert np.array_equal(vq, small.execute(to_device(y)).cpu().numpy())
+    small.close()
