@@ -112,7 +112,9 @@ pfb_status grow_plan_workspace(const Plan &plan, size_t bytes, cudaStream_t stre
     std::lock_guard<std::mutex> lk(mp.stage_mu);
     if (mp.ws2_bytes >= bytes) return PFB_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    const cudaError_t ce = cudaStreamIsCapturing(stream, &cs);
+    if (ce != cudaSuccess) cudaGetLastError();
+    else if (cs != cudaStreamCaptureStatusNone)
         return fail(PFB_ERR_UNSUPPORTED, "the plan's workspace would grow inside a stream capture: run a launch "
                                          "of this size before capturing it");
     if (mp.d_ws2) mp.ws2_retired.push_back(mp.d_ws2);  // a captured graph may still read it
