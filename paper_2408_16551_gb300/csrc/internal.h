@@ -129,6 +129,9 @@ struct Plan {
     mutable void *d_ws2 = nullptr;
     mutable size_t ws2_bytes = 0;
     mutable std::vector<void *> ws2_retired;
+    // guards the workspace alone: pfb_execute_host launches while it holds
+    // stage_mu, and a launch may grow the workspace
+    mutable std::mutex ws2_mu;
     Plan *inv = nullptr;
     // host staging for pfb_execute_host
     std::mutex stage_mu;

@@ -109,7 +109,7 @@ __global__ void gen_tw_pass_kernel(float2 *tw, int Ns, int R) {
 // ---------------------------------------------------------------------------
 pfb_status grow_plan_workspace(const Plan &plan, size_t bytes, cudaStream_t stream) {
     Plan &mp = const_cast<Plan &>(plan);
-    std::lock_guard<std::mutex> lk(mp.stage_mu);
+    std::lock_guard<std::mutex> lk(mp.ws2_mu);
     if (mp.ws2_bytes >= bytes) return PFB_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const cudaError_t ce = cudaStreamIsCapturing(stream, &cs);

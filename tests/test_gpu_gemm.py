@@ -391,3 +391,32 @@ def test_two_pass_products_in_a_graph_on_fresh_plans(path, P, variant):
         assert torch.equal(o, w)
     batch.close()
     plan.close()
+
+
+@pytest.mark.timeout(300)
+@pytest.mark.parametrize("path,P,variant", [(pkg.PFB_DFT_GEMM_F32, 256, None), (pkg.PFB_DFT_GEMM_BF16X3, 1024, 2)])
+def test_two_pass_products_through_the_host_entry_points(path, P, variant):
+    """pfb_execute_host and pfb_execute_batch_host on plans whose launches grow
+    the plan's workspace (the host call holds the plan's staging lock while it
+    launches): results equal the device path bit for bit."""
+    T = 16
+
+    def make():
+        p = pkg.Plan(P, T, pkg.PFB_IN_C64, pkg.PFB_WIN_HAMMING, path)
+        if variant is not None:
+            p.variant = variant
+        return p
+
+    plan = make()
+    x = synth.small_stream(P, T, P * (T - 1 + 700) + 9, seed=P + 5).generate()
+    want = plan.execute(to_device(x)).cpu().numpy()
+    plan2 = make()   # fresh: its workspace grows inside the host call
+    got = plan2.execute_host(x)
+    assert np.array_equal(got, want)
+    out = np.zeros_like(want)
+    plan3 = make()
+    pkg.pfb_execute_batch_host([(plan3, x, out)])
+    assert np.array_equal(out, want)
+    for p in (plan, plan2, plan3):
+        assert p.status() == pkg.PFB_OK
+        p.close()
