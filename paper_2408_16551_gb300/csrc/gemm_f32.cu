@@ -11,9 +11,10 @@
 //   a plan-owned workspace, 128-spectrum row blocks of [128][P] complex64 (rows
 //   past a stream's end are zero); k_cgemm_f32 multiplies: a work unit is a
 //   128-spectrum x 128-bin output tile, 256 threads each accumulating an 8 x 8
-//   complex micro-tile (rows ty + 16 i, bins tx + 16 j: conflict-free shared
-//   reads, coalesced stores), the K loop walks 16 branches at a time through a
-//   3-stage ring of 16-byte cp.async copies of the A and W slices.
+//   complex micro-tile (rows ty + 16 i, bin pairs 2 tx + 32 j: 16-byte shared
+//   reads of two branches of A and of two bins of W, conflict-free, and
+//   16-byte coalesced stores), the K loop walks 16 branches at a time through
+//   a 3-stage ring of 16-byte cp.async copies of the A and W slices.
 // Other P (fused): a work unit is a 64-spectrum x BN-bin output tile (BN = 128,
 //   or 64 for P = 64); 256 threads, each accumulating a 4 x BN/16 complex
 //   micro-tile; the K loop walks 16 branches at a time: the FIR computes the
@@ -267,21 +268,28 @@ __global__ void __launch_bounds__(G4_THREADS, 1) k_cgemm_f32(const __grid_consta
             const float2 *As = g4_smem + (kb % G4_NST) * G4_STAGE;
             const float2 *Bs = As + G4_BM * G4_ASTR;
 #pragma unroll
-            for (int kk = 0; kk < G4_BK; ++kk) {
-                float2 av[8], bv[8];
+            for (int kk = 0; kk < G4_BK; kk += 2) {
+                float4 av[8];  // rows ty + 16 i, branches kk and kk + 1
 #pragma unroll
-                for (int i = 0; i < 8; ++i) av[i] = As[(ty + 16 * i) * G4_ASTR + kk];
+                for (int i = 0; i < 8; ++i) av[i] = *reinterpret_cast<const float4 *>(As + (ty + 16 * i) * G4_ASTR + kk);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) bv[j] = Bs[kk * G4_BN + tx + 16 * j];
+                for (int h = 0; h < 2; ++h) {
+                    float4 bq[4];  // bins 2 tx + 32 j .. + 1
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                    for (int j = 0; j < 4; ++j) bq[j] = *reinterpret_cast<const float4 *>(Bs + (kk + h) * G4_BN + 2 * tx + 32 * j);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        acc[i][j].x = fmaf(av[i].x, bv[j].x, acc[i][j].x);
-                        acc[i][j].x = fmaf(-av[i].y, bv[j].y, acc[i][j].x);
-                        acc[i][j].y = fmaf(av[i].x, bv[j].y, acc[i][j].y);
-                        acc[i][j].y = fmaf(av[i].y, bv[j].x, acc[i][j].y);
+                    for (int i = 0; i < 8; ++i) {
+                        const float ax = h ? av[i].z : av[i].x, ay = h ? av[i].w : av[i].y;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float2 &c0 = acc[i][2 * j], &c1 = acc[i][2 * j + 1];
+                            c0.x = fmaf(ax, bq[j].x, c0.x); c0.x = fmaf(-ay, bq[j].y, c0.x);
+                            c0.y = fmaf(ax, bq[j].y, c0.y); c0.y = fmaf(ay, bq[j].x, c0.y);
+                            c1.x = fmaf(ax, bq[j].z, c1.x); c1.x = fmaf(-ay, bq[j].w, c1.x);
+                            c1.y = fmaf(ax, bq[j].w, c1.y); c1.y = fmaf(ay, bq[j].z, c1.y);
+                        }
                     }
+                }
             }
         }
 #pragma unroll
@@ -289,7 +297,9 @@ __global__ void __launch_bounds__(G4_THREADS, 1) k_cgemm_f32(const __grid_consta
             const int64_t s = s0 + ty + 16 * i;
             if (s < d.S) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) store_cs(d.out + s * d.ldo + k0 + tx + 16 * j, acc[i][j]);
+                for (int j = 0; j < 4; ++j)
+                    __stcs(reinterpret_cast<float4 *>(d.out + s * d.ldo + k0 + 2 * tx + 32 * j),
+                           make_float4(acc[i][2 * j].x, acc[i][2 * j].y, acc[i][2 * j + 1].x, acc[i][2 * j + 1].y));
             }
         }
     }
